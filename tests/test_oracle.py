@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle (oracle/), independent of the oracle's own code.
+
+Each check is something the paper's definition (Section 2, Eq. 1) or plain
+mathematics fixes, chosen so that a plausible slip in the oracle -- a dropped
+neighbour, a wrong index, a wrong start/end rule, |x-y| instead of (x-y)^2, a
+transposed query/reference, a wrong tie order in the walk-back -- fails one:
+
+* brute force: the minimum over every warp path, enumerated explicitly;
+* closed forms: N = 1, M = 1, an exact cut of the reference;
+* invariants: prefix of the last row, monotone cost as the reference grows,
+  common shift, power-of-two scaling, orientation;
+* worked examples derived by hand (tests/golden/worked_examples.json);
+* FP64 central differences of the cost against the walk-back path gradient.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2403_06931_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+# --------------------------------------------------------------- brute force --
+
+def brute_force_last_row(x, y):
+    """Minimum path cost ending at each column of the last row, by enumeration.
+
+    Every warp path starts at some (0, s), moves by (1,0), (0,1) or (1,1), and
+    ends at some (n-1, e); each path is generated once and its cost summed
+    cell by cell.  No recurrence is used: minima are taken over whole paths.
+    """
+    n, m = len(x), len(y)
+    best = [None] * m
+
+    def extend(i, j, acc):
+        acc = acc + (x[i] - y[j]) ** 2
+        if i == n - 1 and (best[j] is None or acc < best[j]):
+            best[j] = acc
+        if i + 1 < n:
+            extend(i + 1, j, acc)
+        if j + 1 < m:
+            extend(i, j + 1, acc)
+        if i + 1 < n and j + 1 < m:
+            extend(i + 1, j + 1, acc)
+
+    for s in range(m):
+        extend(0, s, 0)
+    return best
+
+
+SHAPES = [(n, m) for n in range(1, 6) for m in range(1, 6)] + [(6, 4), (4, 6), (2, 7), (7, 2), (6, 6)]
+
+
+@pytest.mark.parametrize("n,m", SHAPES)
+def test_brute_force_integer_exact(oracle_mod, n, m):
+    rng = np.random.default_rng(1000 * n + m)
+    for _ in range(3):
+        x = [int(v) for v in rng.integers(-4, 5, size=n)]
+        y = [int(v) for v in rng.integers(-4, 5, size=m)]
+        bf = brute_force_last_row(x, y)
+        c64, e64, row64 = oracle_mod.forward(np.array(x, dtype=np.int64), np.array(y, dtype=np.int64), last_row=True)
+        cf, ef, rowf = oracle_mod.forward(np.array(x, dtype=np.float64), np.array(y, dtype=np.float64), last_row=True)
+        assert list(row64) == bf
+        assert [float(v) for v in rowf] == [float(v) for v in bf]
+        assert c64 == min(bf) and e64 == bf.index(min(bf))
+        assert cf == min(bf) and ef == bf.index(min(bf))
+
+
+@pytest.mark.parametrize("n,m", [(3, 3), (4, 5), (5, 4), (6, 6)])
+def test_brute_force_float(oracle_mod, n, m):
+    rng = np.random.default_rng(7 * n + m)
+    for _ in range(3):
+        x = rng.standard_normal(n)
+        y = rng.standard_normal(m)
+        bf = brute_force_last_row(list(x), list(y))
+        _, _, row = oracle_mod.forward(x, y, last_row=True)
+        np.testing.assert_allclose(row, bf, rtol=1e-12, atol=1e-14)
+
+
+# --------------------------------------------------------------- closed forms --
+
+def test_single_sample_query(oracle_mod):
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(257)
+    x = np.array([0.37])
+    c, e = oracle_mod.forward(x, y)
+    d2 = (0.37 - y) ** 2
+    assert c == d2.min() and e == int(np.argmin(d2))
+
+
+def test_single_sample_reference(oracle_mod):
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(91)
+    y = np.array([-0.2])
+    c, e = oracle_mod.forward(x, y)
+    assert e == 0
+    assert math.isclose(c, float(np.sum((x + 0.2) ** 2)), rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("o,n", [(0, 50), (123, 200), (700, 300)])
+def test_exact_cut_has_zero_cost(oracle_mod, o, n):
+    w = inputs.tiny(B=1, N=n, M=1000, seed=11)
+    y = w.ref.astype(np.float64)
+    x = y[o:o + n].copy()
+    c, e, row = oracle_mod.forward(x, y, last_row=True)
+    assert c == 0.0
+    assert row[o + n - 1] == 0.0
+    assert e <= o + n - 1 and row[e] == 0.0
+
+
+def test_tied_minimum_takes_smallest_end(oracle_mod):
+    # x = [1]: last row is (1 - y_j)^2 with exact zeros at j = 2 and j = 5
+    y = np.array([3.0, 0.0, 1.0, 2.0, -1.0, 1.0])
+    c, e = oracle_mod.forward(np.array([1.0]), y)
+    assert c == 0.0 and e == 2
+    c, e = oracle_mod.forward(np.array([1], dtype=np.int64), y.astype(np.int64))
+    assert c == 0 and e == 2
+
+
+# ----------------------------------------------------------------- invariants --
+
+def test_last_row_prefix_and_monotone_growth(oracle_mod):
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(40)
+    y = rng.standard_normal(600)
+    _, _, full = oracle_mod.forward(x, y, last_row=True)
+    prev = math.inf
+    for k in (1, 7, 39, 40, 41, 100, 333, 600):
+        c, e, row = oracle_mod.forward(x, y[:k], last_row=True)
+        assert np.array_equal(row, full[:k])
+        assert c <= prev
+        prev = c
+
+
+def test_common_shift_integer_exact(oracle_mod):
+    rng = np.random.default_rng(6)
+    x = rng.integers(-50, 50, size=30)
+    y = rng.integers(-50, 50, size=200)
+    a = oracle_mod.forward(x, y, last_row=True)
+    b = oracle_mod.forward(x + 1234, y + 1234, last_row=True)
+    assert a[0] == b[0] and a[1] == b[1] and np.array_equal(a[2], b[2])
+
+
+def test_common_shift_float(oracle_mod):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(30)
+    y = rng.standard_normal(200)
+    a = oracle_mod.forward(x, y, last_row=True)
+    b = oracle_mod.forward(x + 0.75, y + 0.75, last_row=True)
+    np.testing.assert_allclose(a[2], b[2], rtol=1e-12)
+
+
+def test_power_of_two_scaling_is_quadratic(oracle_mod):
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(25)
+    y = rng.standard_normal(150)
+    a = oracle_mod.forward(x, y, last_row=True)
+    b = oracle_mod.forward(4.0 * x, 4.0 * y, last_row=True)
+    assert b[0] == 16.0 * a[0] and b[1] == a[1]
+    assert np.array_equal(b[2], 16.0 * a[2])
+
+
+def test_orientation_query_vs_reference(oracle_mod):
+    # the query must be the rows: a one-sample query matches anywhere in y,
+    # while a one-sample reference forces every query sample onto it
+    x = np.array([0.0])
+    y = np.array([5.0, 0.0, 5.0])
+    assert oracle_mod.forward(x, y)[0] == 0.0
+    assert oracle_mod.forward(y, x)[0] == 50.0
+
+
+# ----------------------------------------------------------- worked examples --
+
+def _golden_cases():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+def test_worked_examples(oracle_mod, case):
+    x = np.array(case["x"], dtype=np.int64)
+    y = np.array(case["y"], dtype=np.int64)
+    D = np.array(case["D"], dtype=np.int64)
+    c, e, row = oracle_mod.forward(x, y, last_row=True)
+    assert c == case["cost"] and e == case["end"]
+    assert list(row) == list(D[-1])
+    cf, ef, rowf = oracle_mod.forward(x.astype(np.float64), y.astype(np.float64), last_row=True)
+    assert cf == case["cost"] and ef == case["end"] and list(rowf) == list(D[-1].astype(float))
+    # every row of the hand matrix is the last row of the query's prefix
+    for i in range(len(x)):
+        _, _, r = oracle_mod.forward(x[:i + 1], y, last_row=True)
+        assert list(r) == list(D[i])
+    cells, margins = oracle_mod.walkback(x, y, case["end"])
+    assert cells.tolist() == case["path"]
+    assert margins.tolist() == [float(v) for v in case["margins"]]
+    assert oracle_mod.path_is_valid(cells, len(x), len(y), case["end"])
+    assert oracle_mod.path_cost(x, y, cells) == case["cost"]
+    gx, gy = oracle_mod.path_gradient(x, y, cells)
+    assert gx.tolist() == [float(v) for v in case["gradient_x"]]
+    assert gy.tolist() == [float(v) for v in case["gradient_y"]]
+
+
+def test_path_helpers_reject_invalid_paths(oracle_mod):
+    ok = [[2, 4], [1, 3], [1, 2], [0, 1]]
+    assert oracle_mod.path_is_valid(ok, 3, 5, 4)
+    assert not oracle_mod.path_is_valid(ok, 3, 5, 3)                       # wrong end
+    assert not oracle_mod.path_is_valid([[2, 4], [1, 2], [0, 1]], 3, 5, 4)  # jump of two columns
+    assert not oracle_mod.path_is_valid([[2, 4], [1, 3], [1, 2]], 3, 5, 4)  # never reaches row 0
+    assert not oracle_mod.path_is_valid([[2, 4], [1, 3], [0, 3], [0, 2]], 3, 5, 4)  # runs on in row 0
+    lo, hi = oracle_mod.intervals_from_cells(ok, 3)
+    assert lo.tolist() == [1, 2, 4] and hi.tolist() == [1, 3, 4]
+    assert oracle_mod.cells_from_intervals(lo, hi).tolist() == ok
+
+
+def test_walkback_path_cost_equals_min_cost(oracle_mod):
+    w = inputs.tiny(B=6, N=40, M=500, seed=21)
+    for q in range(w.B):
+        x = w.query(q).astype(np.float64)
+        y = w.ref.astype(np.float64)
+        c, e = oracle_mod.forward(x, y)
+        cells, _ = oracle_mod.walkback(x, y, e)
+        assert oracle_mod.path_is_valid(cells, len(x), len(y), e)
+        assert math.isclose(oracle_mod.path_cost(x, y, cells), c, rel_tol=1e-12)
+
+
+# ------------------------------------------------------ finite differences --
+
+def _stable_fd(oracle_mod, x, y, which, k, h, cells):
+    """Central difference of the cost in x[k] (or y[k]); None if the walk-back
+    path changes at either perturbed point (the cost is then not one quadratic
+    piece over [-h, h] and the difference is not a derivative)."""
+    out = []
+    for s in (+1.0, -1.0):
+        xp, yp = x.copy(), y.copy()
+        (xp if which == "x" else yp)[k] += s * h
+        c, e = oracle_mod.forward(xp, yp)
+        cp, _ = oracle_mod.walkback(xp, yp, e)
+        if cp.shape != cells.shape or not np.array_equal(cp, cells):
+            return None
+        out.append(c)
+    return (out[0] - out[1]) / (2.0 * h)
+
+
+def test_gradient_matches_central_differences(oracle_mod):
+    """8 x 64 vs 512 subset, h = 1e-4, elements where the path is stable."""
+    w = inputs.grad_subset()
+    y = w.ref.astype(np.float64)
+    h = 1e-4
+    rng = np.random.default_rng(9)
+    checked = skipped = 0
+    for q in range(w.B):
+        x = w.query(q).astype(np.float64)
+        c, e = oracle_mod.forward(x, y)
+        cells, _ = oracle_mod.walkback(x, y, e)
+        gx, gy = oracle_mod.path_gradient(x, y, cells, g=1.0)
+        scale = max(np.abs(gx).max(), np.abs(gy).max(), 1e-12)
+        on_path = np.unique(cells[:, 1])
+        off_path = np.setdiff1d(np.arange(len(y)), on_path)
+        ys = np.concatenate([on_path, rng.choice(off_path, size=min(16, len(off_path)), replace=False)])
+        for which, ks in (("x", range(len(x))), ("y", ys)):
+            for k in ks:
+                fd = _stable_fd(oracle_mod, x, y, which, int(k), h, cells)
+                if fd is None:
+                    skipped += 1
+                    continue
+                an = (gx if which == "x" else gy)[int(k)]
+                assert abs(fd - an) <= 1e-6 * scale + 1e-8, (q, which, k, fd, an)
+                checked += 1
+    assert checked > 10 * skipped and checked > 500
+
+
+# --------------------------------------------------------------- integer mode --
+
+def test_int_and_double_oracles_agree_on_int8_codes(oracle_mod):
+    w = inputs.paper_i8(B=6, N=60, M=1500)
+    c_i, e_i = oracle_mod.forward_batch(w.ref, w.queries)
+    c_f, e_f = oracle_mod.forward_batch(w.ref.astype(np.float64), w.queries.astype(np.float64))
+    assert c_i.dtype == np.int64
+    assert np.array_equal(c_i.astype(np.float64), c_f) and np.array_equal(e_i, e_f)
+
+
+def test_batch_driver_matches_single_calls(oracle_mod):
+    w = inputs.ragged_fp32(B=5, n_lo=3, n_hi=40, M=300)
+    costs, ends = oracle_mod.forward_batch(w.ref, w.queries, offsets=w.offsets, threads=3)
+    for q in range(w.B):
+        c, e = oracle_mod.forward(w.query(q), w.ref)
+        assert costs[q] == c and ends[q] == e
+
+
+def test_oracle_rejects_bad_sizes(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.forward(np.zeros(0), np.zeros(4))
+    with pytest.raises(ValueError):
+        oracle_mod.walkback(np.zeros(3), np.zeros(4), 4)
