@@ -1,0 +1,473 @@
+"""Throughput of batched subsequence DTW on one GB300 (or N, one rank each).
+
+Step = one differentiable pass over the paper's batch (Section 6: 512 queries
+of 2,000 samples against a 100,000-sample reference, z-normalised random
+walks): sdtw_forward (cost and end of every query, checkpoints kept) followed
+by sdtw_backward (walk-back gradients w.r.t. queries and reference), through
+the C ABI with device-resident inputs.  value = GCUPS of that step
+(B*N*M cells / step seconds); the forward alone, the backward alone, the int8
+mode and the ragged persistent form (2,048 queries of U[200,4000] samples vs
+1,000,000, one persistent launch replayed from a CUDA graph) are reported
+beside it under "forms".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64, all host cores) on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank runs its own
+batch (weak scaling); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS fwd/bwd, 512×2000 queries vs 100k ref, 1 GB300; % ALU roofline; vs host oracle"
+OPS_PER_CELL = 6          # instruction-issue roofline: ops per DP cell (subtract, 2 min, FMA + overheads)
+LANES_PER_SM = 128        # 4 schedulers x 32 lanes
+L2_FLUSH_BYTES = 512 << 20
+
+# ncu DRAM traffic of one forward launch on the paper batch, valid only while
+# the forward kernel source hashes to FWD_SRC_SHA (else reported as null)
+FWD_SRC_SHA = None
+FWD_TRAFFIC_BYTES = None
+
+
+def src_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        sm = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": seen}
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_06931_gb300 import build as libbuild
+    from paper_2403_06931_gb300 import capi, inputs
+    from paper_2403_06931_gb300.sdtw import SdtwContext
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    w = inputs.paper_fp32(seed=inputs.SEED_BASE + 2 + rank)
+    B, N, M = w.B, w.N, w.M
+    cells = B * N * M
+    ref = torch.from_numpy(w.ref).to(dev)
+    qs = torch.from_numpy(w.queries).to(dev)
+    cost = torch.empty(B, device=dev)
+    end = torch.empty(B, dtype=torch.int64, device=dev)
+    gc = torch.ones(B, device=dev)
+    gq = torch.empty_like(qs)
+    gr = torch.empty_like(ref)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N, grad=True, keep_checkpoints=True)
+    tuned = ctx.autotune(ref, qs)
+    h = ctx.handle
+    P = lambda t: t.data_ptr()  # noqa: E731
+
+    def fwd():
+        capi.check(capi.sdtw_forward(h, P(ref), M, P(qs), None, B, N, P(cost), P(end), sp), "sdtw_forward", h)
+
+    def bwd():
+        capi.check(capi.sdtw_backward(h, P(ref), M, P(qs), None, B, N, P(end), P(gc), P(gq), P(gr), None, sp),
+                   "sdtw_backward", h)
+
+    def step():
+        fwd()
+        bwd()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.device_status() != capi.SDTW_OK:
+        raise RuntimeError("device status error during warm-up")
+
+    # timed region: K steps, L2 flushed before each (outside the events)
+    e_f0, e_f1, e_b1 = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)], \
+        [ev() for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            e_f0[k].record(stream)
+            fwd()
+            e_f1[k].record(stream)
+            bwd()
+            e_b1[k].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    fwd_ms = [e_f0[k].elapsed_time(e_f1[k]) for k in range(args.steps)]
+    bwd_ms = [e_f1[k].elapsed_time(e_b1[k]) for k in range(args.steps)]
+    step_ms = sum(fwd_ms) / args.steps + sum(bwd_ms) / args.steps
+    if ctx.device_status() != capi.SDTW_OK:
+        raise RuntimeError("device status error in the timed region")
+    t = torch.tensor([step_ms], dtype=torch.float64)
+    if world > 1:
+        t = t.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t.item())
+    clocks = clk.summary()
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    href = w.ref.copy()
+    hq = w.queries.copy()
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    t_ref, t_q, t_gc = pin(href), pin(hq), pin(np.ones(B, np.float32))
+    t_cost, t_end = pin(np.empty(B, np.float32)), pin(np.empty(B, np.int64))
+    t_gq, t_gr = pin(np.empty_like(hq)), pin(np.empty_like(href))
+    e2e_ctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N, grad=True, keep_checkpoints=True)
+
+    def e2e_step():
+        capi.check(capi.sdtw_forward_backward_host(
+            e2e_ctx.handle, P(t_ref), M, P(t_q), None, B, N, P(t_gc), P(t_cost), P(t_end), P(t_gq), P(t_gr), None,
+            sp), "sdtw_forward_backward_host", e2e_ctx.handle)
+
+    e2e_ctx.autotune(ref, qs)
+    for _ in range(2):
+        e2e_step()
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ctx.close()
+    h2d = href.nbytes + hq.nbytes + 4 * B
+    d2h = 4 * B + 8 * B + hq.nbytes + href.nbytes
+
+    forms = {}
+    if rank == 0 and not args.no_forms:
+        forms = run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev)
+
+    ctx.close()
+    if rank != 0:
+        return None
+
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_gcups = sms * LANES_PER_SM * f_max * 1e6 / OPS_PER_CELL / 1e9
+    fwd_avg = sum(fwd_ms) / len(fwd_ms)
+    achieved = cells / (fwd_avg * 1e-3) / 1e9
+    fwd_src = os.path.join(ROOT, "paper_2403_06931_gb300", "csrc", "sdtw_forward.cu")
+    traffic = FWD_TRAFFIC_BYTES if FWD_SRC_SHA == src_sha(fwd_src) else None
+    roof = {"bound": "alu", "kernel": "fwd_chain_kernel", "achieved": round(achieved, 1),
+            "peak": round(peak_gcups, 1), "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4),
+            "traffic": traffic,
+            "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {f_max:.0f} MHz ({pk_kind} max SM clock) "
+                          f"/ {OPS_PER_CELL} ops per cell"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = round(achieved / (sms * LANES_PER_SM * clocks["sm_mhz"] * 1e6
+                                                          / OPS_PER_CELL / 1e9), 4)
+    value = world * cells / (step_ms_max * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms_max, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"sdtw_fp32_{B}x{N}_vs_{M}: forward (cost, end, checkpoints) + backward "
+                               "(walk-back gradients)", "B": B, "N": N, "M": M, "cells_per_step": cells,
+                   "plan": tuned, "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}, no collective on the data path"},
+        "fwd_gcups": round(cells / (fwd_avg * 1e-3) / 1e9, 2),
+        "bwd_gcups": round(cells / (sum(bwd_ms) / len(bwd_ms) * 1e-3) / 1e9, 2),
+        "fwd_ms": round(fwd_avg, 3), "bwd_ms": round(sum(bwd_ms) / len(bwd_ms), 3),
+        "wall_ms_per_step_incl_flush": round(t_wall * 1e3 / args.steps, 3),
+        "roofline": roof,
+        "e2e": {"value": round(cells / (statistics.median(e2e_ms) * 1e-3) / 1e9, 2), "unit": "GCUPS",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(statistics.median(e2e_ms), 3),
+                "api": "sdtw_forward_backward_host (pinned host buffers)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "forms": forms,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, w)
+    return out
+
+
+def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
+    """Forward alone, int8 forward, and the ragged persistent form under a CUDA graph."""
+    import torch
+
+    from paper_2403_06931_gb300 import capi, inputs
+    from paper_2403_06931_gb300.sdtw import SdtwContext
+
+    forms = {}
+    B, N, M = w.B, w.N, w.M
+    cells = B * N * M
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    # forward only, no checkpoints
+    fctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N)
+    fplan = fctx.autotune(ref, qs)
+    fctx.forward(ref, qs, out=(cost, end))
+    ms = timed(lambda: fctx.forward(ref, qs, out=(cost, end)), 5)
+    forms["forward_f32"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": fplan}
+    fctx.close()
+
+    # int8 inputs, int32 costs
+    wi = inputs.paper_i8()
+    ri = torch.from_numpy(wi.ref).to(dev)
+    qi = torch.from_numpy(wi.queries).to(dev)
+    ci = torch.empty(B, dtype=torch.int32, device=dev)
+    ictx = SdtwContext(dtype="i8", max_ref_len=M, max_batch=B, max_query_len=N)
+    iplan = ictx.autotune(ri, qi)
+    ictx.forward(ri, qi, out=(ci, end))
+    ms = timed(lambda: ictx.forward(ri, qi, out=(ci, end)), 5)
+    forms["forward_i8"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": iplan}
+    ictx.close()
+
+    if not args.no_ragged:
+        wr = inputs.ragged_fp32()
+        Nr = int(wr.lengths.max())
+        rr = torch.from_numpy(wr.ref).to(dev)
+        qr = torch.from_numpy(wr.queries).to(dev)
+        orr = torch.from_numpy(wr.offsets).to(dev)
+        cr = torch.empty(wr.B, device=dev)
+        er = torch.empty(wr.B, dtype=torch.int64, device=dev)
+        rctx = SdtwContext(max_ref_len=wr.M, max_batch=wr.B, max_query_len=Nr, max_total_query_len=qr.numel())
+        rplan = rctx.autotune(rr, qr, offsets=orr, N=Nr)
+        rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
+        g.replay()
+        torch.cuda.synchronize()
+        ms = timed(g.replay, 3)
+        assert rctx.device_status() == capi.SDTW_OK
+        forms["ragged_persistent_graph"] = {
+            "workload": wr.name, "cells": wr.cells, "gcups": round(wr.cells / (ms * 1e-3) / 1e9, 2),
+            "ms": round(ms, 3), "plan": rplan, "launch": "one persistent kernel, replayed from a CUDA graph"}
+        rctx.close()
+    return forms
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 8 << 30
+
+
+def walkback_threads(w, threads):
+    """Concurrent walk-backs allowed: each holds an N x M double matrix; use at
+    most a quarter of the host's available memory."""
+    per = 8 * w.N * w.M
+    return max(1, min(threads, int(0.25 * mem_available_bytes() // per)))
+
+
+def oracle_step(w, idx, threads):
+    """The oracle's differentiable step on queries idx: forward (cost, end) on
+    all threads, then walk-back over the filled matrix and the path gradient
+    (memory-bounded concurrency)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    y = w.ref.astype(np.float64)
+    xs = [w.query(q).astype(np.float64) for q in idx]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        fw = list(ex.map(lambda x: oracle.forward(x, y), xs))
+
+    def back(k):
+        cells, _ = oracle.walkback(xs[k], y, fw[k][1])
+        return oracle.path_gradient(xs[k], y, cells)
+
+    with ThreadPoolExecutor(max_workers=walkback_threads(w, threads)) as ex:
+        list(ex.map(back, range(len(idx))))
+
+
+def host_threads():
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+
+
+def sample_size(threads):
+    return max(1, min(threads, 16))
+
+
+def cpu_baseline(args, w=None):
+    from paper_2403_06931_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = w or inputs.paper_fp32()
+    threads = min(host_threads(), 16)
+    k = sample_size(threads)
+    idx = list(range(k))
+    t0 = time.perf_counter()
+    oracle_step(w, idx, threads)
+    dt = time.perf_counter() - t0
+    cells = k * w.N * w.M
+    return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{k} of {w.B} queries ({w.N} x {w.M}): FP64 forward on {threads} threads, then walk-back "
+                      f"+ path gradient on {walkback_threads(w, threads)} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    from paper_2403_06931_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = inputs.paper_fp32()
+    threads = min(host_threads(), 16)
+    k = sample_size(threads)
+    idx = list(range(k))
+    for _ in range(args.warmup):
+        oracle_step(w, idx[:1], 1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, idx, threads)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    cells = k * w.N * w.M
+    v = round(cells / (ms * 1e-3) / 1e9, 4)
+    return {"metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"sdtw_fp32_{w.B}x{w.N}_vs_{w.M}: oracle forward + walk-back gradient, "
+                                   f"{k}-query sample per step", "B": w.B, "N": w.N, "M": w.M},
+            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                             "sample": f"{k} of {w.B} queries per step, warm-up on 1 query"},
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-forms", action="store_true", help="skip the forward/int8/ragged side measurements")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged persistent form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

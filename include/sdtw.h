@@ -1,0 +1,238 @@
+/*
+ * sdtw.h -- C ABI of the GB300 (sm_103a) batched subsequence-DTW library.
+ *
+ * The operation (paper Section 2, Eq. 1): a query x of length N (one DP row per
+ * sample) is aligned against a reference y of length M (one DP column per
+ * sample) by
+ *
+ *     D(i,j) = d(x_i, y_j) + min{ D(i-1,j), D(i,j-1), D(i-1,j-1) },
+ *     d(x,y) = (x - y)^2,
+ *
+ * with a free start in the reference (row 0 holds only the local cost,
+ * D(0,j) = d(x_0, y_j)) and a free end: each query returns
+ * cost = min_j D(N-1, j) and end = the smallest j attaining it.  Column 0 has
+ * only the cell above.  A batch holds many queries against one reference, as
+ * in the paper's runSDTW (Section 5): the queries are stored back to back,
+ * with no gaps or metadata (Section 5.1), either all of one length N or, with
+ * an offsets array, of different lengths.
+ *
+ * Conventions shared by every entry point:
+ *   - Device pointers are CUDA global-memory addresses on the context's device;
+ *     the caller owns every buffer it passes and keeps it alive until the work
+ *     queued on `stream` has finished.  Host pointers are ordinary (preferably
+ *     pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device-pointer calls are asynchronous: they validate, queue
+ *     kernels on `stream` and return.  Host-pointer calls return after their
+ *     results are in host memory.
+ *   - A status other than SDTW_OK means nothing was queued, except SDTW_E_CUDA
+ *     returned after a failed launch.  No C++ exception crosses this ABI.
+ *   - Errors found on the device (a query longer than N in a ragged batch, an
+ *     end index out of range) are recorded in the context's device status word
+ *     and reported by sdtw_last_device_status; the affected query's outputs are
+ *     left unwritten.
+ *   - A context is not thread-safe: use one context per host thread / stream.
+ *   - Inputs must be finite.  Inputs are used as given; z-normalisation (the
+ *     paper's Eq. 2) is the caller's step.
+ */
+#ifndef SDTW_H
+#define SDTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDTW_ABI_VERSION 1
+
+typedef struct sdtw_ctx sdtw_ctx;
+
+typedef enum sdtw_status {
+    SDTW_OK = 0,
+    SDTW_E_INVALID = 1,     /* bad argument (null pointer, N<1, M<1, B<0, dtype mismatch, size over a configured maximum) */
+    SDTW_E_NOMEM = 2,       /* device or host workspace could not be allocated, or would exceed mem_cap_bytes */
+    SDTW_E_CUDA = 3,        /* a CUDA runtime call failed; the CUDA error text is kept in the context */
+    SDTW_E_TIMEOUT = 4,     /* a bounded device-side wait ran out (reported by sdtw_last_device_status) */
+    SDTW_E_UNSUPPORTED = 5  /* a valid request this build does not implement (e.g. backward in int8 mode) */
+} sdtw_status;
+
+typedef enum sdtw_dtype {
+    SDTW_F32 = 0, /* float inputs, float costs, FP32 arithmetic (fused multiply-add) */
+    SDTW_I8 = 1   /* int8 inputs, int32 costs, exact integer arithmetic */
+} sdtw_dtype;
+
+/* sdtw_config.flags */
+#define SDTW_FLAG_GRAD 0x1u             /* the context will run sdtw_backward: size checkpoint workspace */
+#define SDTW_FLAG_KEEP_CHECKPOINTS 0x2u /* sdtw_forward also stores the checkpoints sdtw_backward needs */
+#define SDTW_FLAG_NO_AUTOTUNE 0x4u      /* use the built-in default plan instead of timing candidates */
+
+typedef struct sdtw_config {
+    sdtw_dtype dtype;
+    int32_t device;              /* CUDA device ordinal */
+    int64_t max_ref_len;         /* largest M that will be passed */
+    int64_t max_total_query_len; /* largest total query samples per call (B*N, or offsets[B]) */
+    int32_t max_batch;           /* largest B */
+    int32_t max_query_len;       /* largest N (the longest query of a ragged batch) */
+    int32_t seg_width;           /* reference columns per thread (the paper's segment width); 0 = chosen by the library */
+    int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
+    int32_t ckpt_stride;         /* columns between backward checkpoints; 0 = chosen under mem_cap_bytes */
+    int32_t reserved;
+    size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
+    uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
+    uint32_t flags;              /* SDTW_FLAG_* */
+    uint32_t reserved2;
+} sdtw_config;
+
+/* Description of how a call of a given shape will run (for reports and tests). */
+typedef struct sdtw_plan {
+    int32_t seg_width;       /* W: reference columns per thread */
+    int32_t warps_per_query; /* P: warps in one query's chain of threads */
+    int32_t ctas_per_query;  /* CTAs in one query's chain (thread-block cluster size) */
+    int32_t persistent;      /* 1 if one persistent launch pulls queries from a device queue */
+    int64_t grid;            /* CTAs launched */
+    int32_t block;           /* threads per CTA */
+    int32_t smem_bytes;      /* dynamic shared memory per CTA */
+    int32_t ckpt_stride;     /* K: columns between checkpoints (0 when none are stored) */
+    int32_t tuned;           /* 1 if chosen by timing candidates, 0 if the default */
+    int64_t sweep_cols;      /* reference columns covered by one sweep of the chain */
+} sdtw_plan;
+
+/* ABI version this library was built with (SDTW_ABI_VERSION). */
+int32_t sdtw_abi_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* sdtw_status_string(sdtw_status s);
+
+/* Fill *cfg with defaults: F32, device 0, maxima of the paper's batch
+ * (512 x 2000 vs 100,000), everything else chosen by the library.
+ * Errors: SDTW_E_INVALID if cfg is NULL. */
+sdtw_status sdtw_config_init(sdtw_config* cfg);
+
+/* Create a context on cfg->device.  The context owns its device workspace
+ * (status word, work queue, checkpoints and gradient scratch when
+ * SDTW_FLAG_GRAD is set), sized from the cfg maxima and allocated here.
+ * *out receives the context, or NULL on error.
+ * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
+ * SDTW_FLAG_GRAD with SDTW_I8), SDTW_E_NOMEM (workspace above mem_cap_bytes or
+ * allocation failure), SDTW_E_CUDA (device unusable). */
+sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg);
+
+/* Release the context and its workspace (synchronises its device first).
+ * NULL is accepted.  Returns SDTW_OK or SDTW_E_CUDA. */
+sdtw_status sdtw_destroy(sdtw_ctx* ctx);
+
+/*
+ * Forward sDTW of a batch (Section 2, Eq. 1; batch layout of Section 5).
+ *   ref      device, M elements: float (SDTW_F32) or int8 (SDTW_I8).
+ *   queries  device: uniform batch [B][N] row-major when offsets == NULL;
+ *            ragged batch of offsets[B] elements when offsets != NULL
+ *            (query q = queries[offsets[q] .. offsets[q+1])).  Same element
+ *            type as ref.
+ *   offsets  device int64 [B+1], non-decreasing, offsets[0] = 0, or NULL.
+ *            Ragged queries must be no longer than N; an empty query returns
+ *            cost = +inf (SDTW_F32) or INT32_MAX (SDTW_I8) and end = -1.
+ *   B        number of queries (0 is a no-op).  N: the query length (uniform)
+ *            or an upper bound on every query length (ragged).  M >= 1.
+ *   cost     device, B elements: float (SDTW_F32) or int32 (SDTW_I8).
+ *   end      device int64, B elements: the smallest column of the minimum.
+ * With SDTW_FLAG_KEEP_CHECKPOINTS the call also stores the checkpoints a
+ * following sdtw_backward on the same arguments reuses.
+ * Errors: SDTW_E_INVALID (null pointers with B > 0, N < 1, M < 1, sizes above
+ * the context maxima; SDTW_I8 needs N <= 33,000 so int32 costs cannot
+ * overflow), SDTW_E_UNSUPPORTED (N too long for shared memory), SDTW_E_CUDA.
+ */
+sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
+                         const int64_t* offsets, int32_t B, int32_t N, void* cost, int64_t* end,
+                         void* stream);
+
+/*
+ * Gradient of sum_q grad_cost[q] * cost[q] (SDTW_F32 only).
+ * The warp path of each query is recovered by walking back from (N_q-1, end[q])
+ * (Section 2's walk-back: to the neighbour (i-1,j-1), (i,j-1) or (i-1,j) of
+ * smallest D, exact ties to the first of that list, column 0 upwards, stopping
+ * at row 0).  The DP is recomputed block by block from column checkpoints
+ * stored every ckpt_stride columns; the full matrix is never stored.
+ * Along the path, d cost/d x_i += 2 (x_i - y_j) and d cost/d y_j += -2 (x_i - y_j).
+ *   ref, queries, offsets, B, N, M: as in sdtw_forward (float).
+ *   end         device int64 [B]: the end columns sdtw_forward returned.
+ *   grad_cost   device float [B]: upstream gradient of each cost.
+ *   grad_queries device float, same layout as queries: overwritten.
+ *   grad_ref    device float [M]: overwritten with the sum over queries
+ *               (summed in query order: deterministic).
+ *   path        device int32, NULL or 2 per query sample: for row i of query q
+ *               the first and last column of the path in that row
+ *               (path[2*(start_q+i)] and path[2*(start_q+i)+1], start_q = q*N or
+ *               offsets[q]).  A warp path is monotone, so this fixes it.
+ * If the context has SDTW_FLAG_KEEP_CHECKPOINTS and the previous sdtw_forward
+ * on this context had the same ref/queries/offsets pointers and sizes, its
+ * checkpoints are reused: the caller must not have changed those inputs.
+ * Otherwise the forward is re-run with checkpoint stores first.
+ * Errors: SDTW_E_UNSUPPORTED (SDTW_I8 context), SDTW_E_INVALID (no
+ * SDTW_FLAG_GRAD, bad arguments as for sdtw_forward), SDTW_E_NOMEM, SDTW_E_CUDA.
+ */
+sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries,
+                          const int64_t* offsets, int32_t B, int32_t N, const int64_t* end,
+                          const float* grad_cost, float* grad_queries, float* grad_ref,
+                          int32_t* path, void* stream);
+
+/*
+ * sdtw_forward from and to host memory (the paper's runSDTW shape: host batch
+ * in, host results out).  Copies ref/queries/offsets into context-owned
+ * device buffers, runs the forward, copies cost/end back and synchronises
+ * `stream`.  Pointers are host pointers with the layouts of sdtw_forward.
+ * Errors: as sdtw_forward, plus SDTW_E_NOMEM when staging buffers cannot grow.
+ */
+sdtw_status sdtw_forward_host(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
+                              const int64_t* offsets, int32_t B, int32_t N, void* cost,
+                              int64_t* end, void* stream);
+
+/*
+ * One differentiable step from and to host memory: forward and backward on
+ * staged copies of ref/queries, then cost, end, grad_queries and grad_ref
+ * (and path if not NULL) copied back; synchronises `stream`.  grad_cost is a
+ * host float [B].  Needs an SDTW_F32 context with SDTW_FLAG_GRAD.
+ * Errors: as sdtw_forward and sdtw_backward.
+ */
+sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t M,
+                                       const float* queries, const int64_t* offsets, int32_t B,
+                                       int32_t N, const float* grad_cost, float* cost,
+                                       int64_t* end, float* grad_queries, float* grad_ref,
+                                       int32_t* path, void* stream);
+
+/*
+ * Time the candidate plans (segment width, warps per query, chain length) on
+ * the given device-resident batch and keep the fastest for calls of this
+ * shape class (dtype, ragged or not, N and M buckets) on this context.
+ * Runs several forwards on `stream` and synchronises it.  Arguments as
+ * sdtw_forward; cost/end are scratch outputs.  *plan (if not NULL) receives
+ * the chosen plan.  Errors: as sdtw_forward.
+ */
+sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
+                          const int64_t* offsets, int32_t B, int32_t N, void* cost,
+                          int64_t* end, void* stream, sdtw_plan* plan);
+
+/* The plan a forward (backward = 0) or backward (backward = 1) call of this
+ * shape would use.  ragged = 1 for a call with offsets.  No device work.
+ * Errors: SDTW_E_INVALID. */
+sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_t ragged,
+                          int32_t backward, sdtw_plan* plan);
+
+/* Synchronise `stream`, then return and clear the device status word: SDTW_OK,
+ * SDTW_E_INVALID (a ragged query longer than N, an end index outside [0, M))
+ * or SDTW_E_TIMEOUT.  SDTW_E_CUDA if the synchronisation itself failed. */
+sdtw_status sdtw_last_device_status(sdtw_ctx* ctx, void* stream);
+
+/* Text of the last CUDA error this context saw ("" if none); valid until the
+ * next call on the context. */
+const char* sdtw_last_error(sdtw_ctx* ctx);
+
+/* Bytes of device workspace the context currently holds. */
+size_t sdtw_workspace_bytes(sdtw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDTW_H */

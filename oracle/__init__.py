@@ -220,3 +220,61 @@ def intervals_from_cells(cells, n: int):
         lo[i] = j if lo[i] < 0 else min(lo[i], j)
         hi[i] = max(hi[i], j)
     return lo, hi
+
+
+# ------------------------------------------------- per-row interval form --
+# A monotone warp path visits, in each row i, one contiguous run of columns
+# [lo_i, hi_i].  The helpers below evaluate the same definitions as
+# path_is_valid / path_cost / path_gradient on that form without expanding
+# the cells (the sums over a run use prefix sums of y and y^2, in double).
+
+def intervals_are_valid(lo, hi, m: int, end: int) -> bool:
+    """Runs of a valid warp path ending at (n-1, end): 0 <= lo_i <= hi_i < m,
+    hi_{n-1} = end, and between rows the path steps up (lo_i = hi_{i-1}) or
+    diagonally (lo_i = hi_{i-1} + 1)."""
+    lo = np.asarray(lo, dtype=np.int64)
+    hi = np.asarray(hi, dtype=np.int64)
+    if lo.shape != hi.shape or lo.ndim != 1 or lo.size < 1:
+        return False
+    if (lo < 0).any() or (hi >= m).any() or (lo > hi).any() or hi[-1] != end:
+        return False
+    step = lo[1:] - hi[:-1]
+    return bool(((step == 0) | (step == 1)).all())
+
+
+def intervals_cost(x, y, lo, hi) -> float:
+    """sum_i sum_{j=lo_i..hi_i} (x_i - y_j)^2 in double."""
+    xa = np.asarray(x, dtype=np.float64)
+    ya = np.asarray(y, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.int64)
+    hi = np.asarray(hi, dtype=np.int64)
+    s1 = np.concatenate([[0.0], np.cumsum(ya)])
+    s2 = np.concatenate([[0.0], np.cumsum(ya * ya)])
+    cnt = (hi - lo + 1).astype(np.float64)
+    sy = s1[hi + 1] - s1[lo]
+    syy = s2[hi + 1] - s2[lo]
+    return float(np.sum(cnt * xa * xa - 2.0 * xa * sy + syy))
+
+
+def intervals_gradient(x, y, lo, hi, g: float = 1.0):
+    """Gradient of g * intervals_cost: d/dx_i = 2 g sum_j (x_i - y_j) over the
+    row's run; d/dy_j = -2 g sum over rows whose run covers j of (x_i - y_j)."""
+    xa = np.asarray(x, dtype=np.float64)
+    ya = np.asarray(y, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.int64)
+    hi = np.asarray(hi, dtype=np.int64)
+    m = ya.shape[0]
+    s1 = np.concatenate([[0.0], np.cumsum(ya)])
+    cnt = (hi - lo + 1).astype(np.float64)
+    gx = 2.0 * g * (cnt * xa - (s1[hi + 1] - s1[lo]))
+    # rows covering column j: difference arrays of the count and of sum x_i
+    dc = np.zeros(m + 1)
+    dx = np.zeros(m + 1)
+    np.add.at(dc, lo, 1.0)
+    np.add.at(dc, hi + 1, -1.0)
+    np.add.at(dx, lo, xa)
+    np.add.at(dx, hi + 1, -xa)
+    c = np.cumsum(dc)[:m]
+    sx = np.cumsum(dx)[:m]
+    gy = -2.0 * g * (sx - c * ya)
+    return gx, gy

@@ -1,0 +1,660 @@
+// C ABI of the sDTW library (include/sdtw.h): contexts, argument checks,
+// device workspace, launch plans and the autotuner, host-buffer entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sdtw.h"
+#include "sdtw_internal.h"
+
+using sdtw::FwdArgs;
+using sdtw::FwdPlan;
+
+namespace {
+
+constexpr size_t kDefaultCap = size_t(16) << 30;
+constexpr int kMaxSmem = 227 * 1024;
+constexpr int kI8MaxN = 33000;  // N * 254^2 < 2^31
+constexpr int kBwdStrides[] = {64, 128, 256};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// shape class a tuned plan applies to
+struct TuneKey {
+    int dtype, ragged, nbucket, mbucket, ckpt;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(dtype, ragged, nbucket, mbucket, ckpt) <
+               std::tie(o.dtype, o.ragged, o.nbucket, o.mbucket, o.ckpt);
+    }
+};
+
+int bucket_of(int64_t v)
+{
+    int b = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+struct CkptKey {
+    const void* ref = nullptr;
+    const void* queries = nullptr;
+    const int64_t* offsets = nullptr;
+    int64_t M = 0;
+    int32_t B = 0, N = 0;
+    int32_t K = 0;
+    bool valid = false;
+};
+
+}  // namespace
+
+struct sdtw_ctx {
+    sdtw_config cfg{};
+    int sm_count = 0;
+    std::string err;
+    size_t cap = kDefaultCap;
+    size_t ws_bytes = 0;
+
+    int* d_status = nullptr;
+    int* d_queue = nullptr;
+    int32_t* d_order = nullptr;
+
+    // backward workspace
+    float* d_ckpt = nullptr;
+    size_t ckpt_elems = 0;
+    int K_min = 0;        // smallest checkpoint stride the workspace holds for a full chunk
+    int K = 0;            // checkpoint stride in use
+    int bwd_chunk = 0;    // queries per backward chunk
+    float* d_gyq = nullptr;
+    int64_t* d_span = nullptr;
+    void* d_cost_tmp = nullptr;
+    int64_t* d_end_tmp = nullptr;
+    CkptKey key;
+
+    // host-call staging
+    DevBuf st_ref, st_q, st_off, st_cost, st_end, st_gc, st_gq, st_gr, st_path;
+
+    std::map<TuneKey, std::pair<int, int>> tuned;  // -> (W, P)
+};
+
+namespace {
+
+sdtw_status cuda_fail(sdtw_ctx* c, cudaError_t e)
+{
+    if (c) c->err = cudaGetErrorString(e);
+    return SDTW_E_CUDA;
+}
+
+size_t elem_size(sdtw_dtype dt) { return dt == SDTW_I8 ? 1 : 4; }
+
+sdtw_status dev_alloc(sdtw_ctx* c, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return SDTW_OK;
+    if (c->ws_bytes + bytes > c->cap) return SDTW_E_NOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        c->err = cudaGetErrorString(e);
+        return SDTW_E_NOMEM;
+    }
+    c->ws_bytes += bytes;
+    return SDTW_OK;
+}
+
+void dev_free(sdtw_ctx* c, void* p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        c->ws_bytes -= bytes;
+    }
+}
+
+sdtw_status ensure(sdtw_ctx* c, DevBuf& b, size_t bytes)
+{
+    if (b.bytes >= bytes && (b.p || bytes == 0)) return SDTW_OK;
+    dev_free(c, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+    sdtw_status s = dev_alloc(c, &b.p, bytes);
+    if (s == SDTW_OK) b.bytes = bytes;
+    return s;
+}
+
+int64_t nblk_of(int64_t M, int K) { return K > 0 ? M / K : 0; }
+
+// default plan for a forward call
+FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
+{
+    FwdPlan p;
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 16;
+    p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 8;
+    auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
+    if (it != c->tuned.end() && c->cfg.seg_width <= 0 && c->cfg.warps_per_query <= 0) {
+        p.W = it->second.first;
+        p.P = it->second.second;
+    }
+    // a short reference needs fewer threads per query (unless the caller fixed P)
+    if (c->cfg.warps_per_query <= 0)
+        while (p.P > 1 && static_cast<int64_t>(32) * (p.P / 2) * p.W >= M) p.P /= 2;
+    if (ckpt && c->K % p.W != 0) p.W = 16;
+    p.block = 32 * p.P;
+    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P);
+    p.persistent = ragged;
+    if (p.persistent) {
+        int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem);
+        p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
+    } else {
+        p.grid = B;
+    }
+    return p;
+}
+
+sdtw_status check_common(sdtw_ctx* c, const void* ref, int64_t M, const void* queries, int32_t B, int32_t N,
+                         const void* o1, const void* o2)
+{
+    if (!c) return SDTW_E_INVALID;
+    if (B < 0 || M < 1 || N < 1) return SDTW_E_INVALID;
+    if (M > c->cfg.max_ref_len || N > c->cfg.max_query_len || B > c->cfg.max_batch) return SDTW_E_INVALID;
+    if (M > INT_MAX / 2) return SDTW_E_INVALID;
+    if (B > 0 && (!ref || !queries || !o1 || !o2)) return SDTW_E_INVALID;
+    if (c->cfg.dtype == SDTW_I8 && N > kI8MaxN) return SDTW_E_INVALID;
+    return SDTW_OK;
+}
+
+sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
+                        int32_t B, int32_t N, void* cost, int64_t* end, cudaStream_t s, const FwdPlan* force,
+                        float* ckpt, int32_t q0, int32_t nq)
+{
+    const bool ragged = offsets != nullptr;
+    FwdPlan p = force ? *force : default_fwd_plan(c, nq, N, M, ragged, ckpt != nullptr);
+    if (p.smem > kMaxSmem) return SDTW_E_UNSUPPORTED;
+    if (sdtw::fwd_total_steps(M, N, p.W, p.P) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
+    if (p.persistent) p.grid = std::min(p.grid, nq);
+    else p.grid = nq;
+    FwdArgs a{};
+    a.ref = ref;
+    a.M = M;
+    a.queries = queries;
+    a.offsets = offsets;
+    a.B = nq;
+    a.N = N;
+    a.q0 = q0;
+    a.B_total = B;
+    a.cost = cost;
+    a.end = end;
+    a.ckpt = ckpt;
+    a.K = ckpt ? c->K : 1;
+    a.nblk = ckpt ? nblk_of(M, c->K) : 0;
+    a.ckpt_rows = ckpt ? static_cast<int64_t>(c->bwd_chunk) * c->cfg.max_query_len : 0;
+    a.status = c->d_status;
+    a.queue = nullptr;
+    a.order = nullptr;
+    cudaError_t e;
+    if (p.persistent) {
+        if ((e = cudaMemsetAsync(c->d_queue, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(c, e);
+        if (ragged && q0 == 0 && nq == B) {
+            if ((e = sdtw::launch_order_by_length(offsets, B, c->d_order, s)) != cudaSuccess) return cuda_fail(c, e);
+            a.order = c->d_order;
+        }
+        a.queue = c->d_queue;
+    }
+    if ((e = sdtw::launch_forward(c->cfg.dtype, p, a, s)) != cudaSuccess) return cuda_fail(c, e);
+    return SDTW_OK;
+}
+
+sdtw_status alloc_backward(sdtw_ctx* c)
+{
+    const sdtw_config& f = c->cfg;
+    const int64_t M = f.max_ref_len;
+    const int64_t N = f.max_query_len;
+    int Ks[3];
+    int nK = 0;
+    if (f.ckpt_stride > 0) {
+        if (!sdtw::bwd_stride_supported(f.ckpt_stride)) return SDTW_E_INVALID;
+        Ks[nK++] = f.ckpt_stride;
+    } else {
+        for (int k : kBwdStrides) Ks[nK++] = k;
+    }
+    // cost/end scratch for the forward re-run is sized by max_batch, not by the chunk
+    const size_t fixed = c->ws_bytes + 12 * static_cast<size_t>(f.max_batch);
+    for (int i = 0; i < nK; ++i) {
+        const int K = Ks[i];
+        // per query: checkpoints N*floor(M/K) floats, gradient row M floats, span, cost/end scratch
+        const size_t per_q = 4 * static_cast<size_t>(N) * nblk_of(M, K) + 4 * static_cast<size_t>(M) + 32;
+        if (fixed + per_q > c->cap) continue;
+        const int64_t fit = static_cast<int64_t>((c->cap - fixed) / per_q);
+        const int chunk = static_cast<int>(std::min<int64_t>(fit, f.max_batch));
+        c->K_min = K;
+        c->K = f.ckpt_stride > 0 ? f.ckpt_stride : 256;
+        c->bwd_chunk = chunk;
+        c->ckpt_elems = static_cast<size_t>(N) * nblk_of(M, K) * chunk;
+        sdtw_status s;
+        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_ckpt), 4 * std::max<size_t>(c->ckpt_elems, 1))) != SDTW_OK)
+            return s;
+        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_gyq), 4 * static_cast<size_t>(M) * chunk)) != SDTW_OK)
+            return s;
+        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_span), 16 * static_cast<size_t>(chunk))) != SDTW_OK)
+            return s;
+        if ((s = dev_alloc(c, &c->d_cost_tmp, 4 * static_cast<size_t>(f.max_batch))) != SDTW_OK) return s;
+        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_end_tmp), 8 * static_cast<size_t>(f.max_batch))) != SDTW_OK)
+            return s;
+        return SDTW_OK;
+    }
+    return SDTW_E_NOMEM;
+}
+
+void free_all(sdtw_ctx* c)
+{
+    dev_free(c, c->d_status, sizeof(int));
+    dev_free(c, c->d_queue, sizeof(int));
+    dev_free(c, c->d_order, 4 * static_cast<size_t>(c->cfg.max_batch));
+    dev_free(c, c->d_ckpt, 4 * std::max<size_t>(c->ckpt_elems, 1));
+    dev_free(c, c->d_gyq, 4 * static_cast<size_t>(c->cfg.max_ref_len) * c->bwd_chunk);
+    dev_free(c, c->d_span, 16 * static_cast<size_t>(c->bwd_chunk));
+    dev_free(c, c->d_cost_tmp, 4 * static_cast<size_t>(c->cfg.max_batch));
+    dev_free(c, c->d_end_tmp, 8 * static_cast<size_t>(c->cfg.max_batch));
+    for (DevBuf* b : {&c->st_ref, &c->st_q, &c->st_off, &c->st_cost, &c->st_end, &c->st_gc, &c->st_gq, &c->st_gr,
+                      &c->st_path})
+        dev_free(c, b->p, b->bytes);
+}
+
+bool key_matches(const CkptKey& k, const void* ref, int64_t M, const void* q, const int64_t* off, int32_t B,
+                 int32_t N, int K)
+{
+    return k.valid && k.ref == ref && k.M == M && k.queries == q && k.offsets == off && k.B == B && k.N == N &&
+           k.K == K;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sdtw_abi_version(void) { return SDTW_ABI_VERSION; }
+
+const char* sdtw_status_string(sdtw_status s)
+{
+    switch (s) {
+    case SDTW_OK: return "SDTW_OK";
+    case SDTW_E_INVALID: return "SDTW_E_INVALID: invalid argument";
+    case SDTW_E_NOMEM: return "SDTW_E_NOMEM: workspace allocation failed or over the memory cap";
+    case SDTW_E_CUDA: return "SDTW_E_CUDA: CUDA runtime error";
+    case SDTW_E_TIMEOUT: return "SDTW_E_TIMEOUT: a bounded device wait ran out";
+    case SDTW_E_UNSUPPORTED: return "SDTW_E_UNSUPPORTED: not supported by this build";
+    }
+    return "SDTW: unknown status";
+}
+
+sdtw_status sdtw_config_init(sdtw_config* cfg)
+{
+    if (!cfg) return SDTW_E_INVALID;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->dtype = SDTW_F32;
+    cfg->device = 0;
+    cfg->max_ref_len = 100000;
+    cfg->max_total_query_len = 512 * 2000;
+    cfg->max_batch = 512;
+    cfg->max_query_len = 2000;
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
+{
+    if (!out || !cfg) return SDTW_E_INVALID;
+    *out = nullptr;
+    if (cfg->dtype != SDTW_F32 && cfg->dtype != SDTW_I8) return SDTW_E_INVALID;
+    if (cfg->max_ref_len < 1 || cfg->max_query_len < 1 || cfg->max_batch < 1 || cfg->max_total_query_len < 1)
+        return SDTW_E_INVALID;
+    if (cfg->max_ref_len > INT_MAX / 2) return SDTW_E_INVALID;
+    if ((cfg->flags & (SDTW_FLAG_GRAD | SDTW_FLAG_KEEP_CHECKPOINTS)) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
+    if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
+    if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
+    if (cfg->dtype == SDTW_I8 && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
+
+    sdtw_ctx* c = new (std::nothrow) sdtw_ctx();
+    if (!c) return SDTW_E_NOMEM;
+    c->cfg = *cfg;
+    c->cap = cfg->mem_cap_bytes ? cfg->mem_cap_bytes : kDefaultCap;
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SDTW_E_CUDA;
+    }
+    sdtw_status s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
+    if (s == SDTW_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_queue), sizeof(int));
+    if (s == SDTW_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_order), 4 * static_cast<size_t>(cfg->max_batch));
+    if (s == SDTW_OK && (cfg->flags & SDTW_FLAG_GRAD)) s = alloc_backward(c);
+    if (s == SDTW_OK) {
+        e = cudaMemset(c->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) s = cuda_fail(c, e);
+    }
+    if (s != SDTW_OK) {
+        free_all(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_destroy(sdtw_ctx* ctx)
+{
+    if (!ctx) return SDTW_OK;
+    cudaSetDevice(ctx->cfg.device);
+    cudaError_t e = cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+    return e == cudaSuccess ? SDTW_OK : SDTW_E_CUDA;
+}
+
+sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
+                         int32_t B, int32_t N, void* cost, int64_t* end, void* stream)
+{
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
+    if (s != SDTW_OK) return s;
+    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    if (B == 0) return SDTW_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* ckpt = nullptr;
+    const bool keep = (ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk;
+    if (keep) ckpt = ctx->d_ckpt;
+    ctx->key.valid = false;
+    s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, ckpt, 0, B);
+    if (s == SDTW_OK && keep) {
+        ctx->key.ref = ref;
+        ctx->key.queries = queries;
+        ctx->key.offsets = offsets;
+        ctx->key.M = M;
+        ctx->key.B = B;
+        ctx->key.N = N;
+        ctx->key.K = ctx->K;
+        ctx->key.valid = true;
+    }
+    return s;
+}
+
+sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
+                          int32_t B, int32_t N, const int64_t* end, const float* grad_cost, float* grad_queries,
+                          float* grad_ref, int32_t* path, void* stream)
+{
+    if (!ctx) return SDTW_E_INVALID;
+    if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
+    if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, end, grad_cost);
+    if (s != SDTW_OK) return s;
+    if (B > 0 && (!grad_queries || !grad_ref)) return SDTW_E_INVALID;
+    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    if (sdtw::bwd_smem_bytes(N, ctx->K) > kMaxSmem) return SDTW_E_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (B == 0) {
+        if (!grad_ref) return SDTW_E_INVALID;
+        if ((e = cudaMemsetAsync(grad_ref, 0, 4 * static_cast<size_t>(M), st)) != cudaSuccess) return cuda_fail(ctx, e);
+        return SDTW_OK;
+    }
+    const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N, ctx->K);
+    const int chunk = ctx->bwd_chunk;
+    for (int q0 = 0; q0 < B; q0 += chunk) {
+        const int nq = std::min(chunk, B - q0);
+        if (!reuse) {
+            s = run_forward(ctx, ref, M, queries, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, nullptr,
+                            ctx->d_ckpt, q0, nq);
+            if (s != SDTW_OK) return s;
+        }
+        sdtw::BwdArgs a{};
+        a.ref = ref;
+        a.M = M;
+        a.queries = queries;
+        a.offsets = offsets;
+        a.B = nq;
+        a.N = N;
+        a.q0 = q0;
+        a.B_total = B;
+        a.end = end;
+        a.grad_cost = grad_cost;
+        a.grad_queries = grad_queries;
+        a.path = path;
+        a.ckpt = ctx->d_ckpt;
+        a.K = ctx->K;
+        a.nblk = nblk_of(M, ctx->K);
+        a.ckpt_rows = static_cast<int64_t>(ctx->bwd_chunk) * ctx->cfg.max_query_len;
+        a.gyq = ctx->d_gyq;
+        a.span = ctx->d_span;
+        a.status = ctx->d_status;
+        if ((e = sdtw::launch_backward_walk(a, st)) != cudaSuccess) return cuda_fail(ctx, e);
+        if ((e = sdtw::launch_grad_ref_reduce(ctx->d_gyq, ctx->d_span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
+            return cuda_fail(ctx, e);
+    }
+    if (!reuse) ctx->key.valid = false;
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_forward_host(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
+                              int32_t B, int32_t N, void* cost, int64_t* end, void* stream)
+{
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
+    if (s != SDTW_OK) return s;
+    if (B == 0) return SDTW_OK;
+    const int64_t total = offsets ? offsets[B] : static_cast<int64_t>(B) * N;
+    if (total < 0 || total > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    const size_t es = elem_size(ctx->cfg.dtype);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = ensure(ctx, ctx->st_ref, es * M)) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_q, es * std::max<int64_t>(total, 1))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_cost, 4 * static_cast<size_t>(B))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_end, 8 * static_cast<size_t>(B))) != SDTW_OK) return s;
+    if (offsets && (s = ensure(ctx, ctx->st_off, 8 * static_cast<size_t>(B + 1))) != SDTW_OK) return s;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ctx->st_ref.p, ref, es * M, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(ctx, e);
+    if (total > 0 && (e = cudaMemcpyAsync(ctx->st_q.p, queries, es * total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (offsets &&
+        (e = cudaMemcpyAsync(ctx->st_off.p, offsets, 8 * static_cast<size_t>(B + 1), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return cuda_fail(ctx, e);
+    s = sdtw_forward(ctx, ctx->st_ref.p, M, ctx->st_q.p, offsets ? static_cast<const int64_t*>(ctx->st_off.p) : nullptr,
+                     B, N, ctx->st_cost.p, static_cast<int64_t*>(ctx->st_end.p), stream);
+    if (s != SDTW_OK) return s;
+    if ((e = cudaMemcpyAsync(cost, ctx->st_cost.p, 4 * static_cast<size_t>(B), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if ((e = cudaMemcpyAsync(end, ctx->st_end.p, 8 * static_cast<size_t>(B), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e);
+    ctx->key.valid = false;  // staged inputs are reused by later host calls
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries,
+                                       const int64_t* offsets, int32_t B, int32_t N, const float* grad_cost,
+                                       float* cost, int64_t* end, float* grad_queries, float* grad_ref,
+                                       int32_t* path, void* stream)
+{
+    if (!ctx) return SDTW_E_INVALID;
+    if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
+    if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
+    if (s != SDTW_OK) return s;
+    if (B > 0 && (!grad_cost || !grad_queries)) return SDTW_E_INVALID;
+    if (!grad_ref) return SDTW_E_INVALID;
+    const int64_t total = B == 0 ? 0 : (offsets ? offsets[B] : static_cast<int64_t>(B) * N);
+    if (total < 0 || total > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((s = ensure(ctx, ctx->st_ref, 4 * M)) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_q, 4 * std::max<int64_t>(total, 1))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_cost, 4 * static_cast<size_t>(std::max(B, 1)))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_end, 8 * static_cast<size_t>(std::max(B, 1)))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_gc, 4 * static_cast<size_t>(std::max(B, 1)))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_gq, 4 * std::max<int64_t>(total, 1))) != SDTW_OK) return s;
+    if ((s = ensure(ctx, ctx->st_gr, 4 * M)) != SDTW_OK) return s;
+    if (path && (s = ensure(ctx, ctx->st_path, 8 * std::max<int64_t>(total, 1))) != SDTW_OK) return s;
+    if (offsets && (s = ensure(ctx, ctx->st_off, 8 * static_cast<size_t>(B + 1))) != SDTW_OK) return s;
+    if ((e = cudaMemcpyAsync(ctx->st_ref.p, ref, 4 * M, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(ctx, e);
+    if (total > 0 && (e = cudaMemcpyAsync(ctx->st_q.p, queries, 4 * total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (B > 0 && (e = cudaMemcpyAsync(ctx->st_gc.p, grad_cost, 4 * static_cast<size_t>(B), cudaMemcpyHostToDevice, st)) !=
+                     cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (offsets &&
+        (e = cudaMemcpyAsync(ctx->st_off.p, offsets, 8 * static_cast<size_t>(B + 1), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return cuda_fail(ctx, e);
+    const int64_t* doff = offsets ? static_cast<const int64_t*>(ctx->st_off.p) : nullptr;
+    const float* dref = static_cast<const float*>(ctx->st_ref.p);
+    const float* dq = static_cast<const float*>(ctx->st_q.p);
+    s = sdtw_forward(ctx, dref, M, dq, doff, B, N, ctx->st_cost.p, static_cast<int64_t*>(ctx->st_end.p), stream);
+    if (s != SDTW_OK) return s;
+    s = sdtw_backward(ctx, dref, M, dq, doff, B, N, static_cast<const int64_t*>(ctx->st_end.p),
+                      static_cast<const float*>(ctx->st_gc.p), static_cast<float*>(ctx->st_gq.p),
+                      static_cast<float*>(ctx->st_gr.p), path ? static_cast<int32_t*>(ctx->st_path.p) : nullptr, stream);
+    if (s != SDTW_OK) return s;
+    if (B > 0) {
+        if ((e = cudaMemcpyAsync(cost, ctx->st_cost.p, 4 * static_cast<size_t>(B), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if ((e = cudaMemcpyAsync(end, ctx->st_end.p, 8 * static_cast<size_t>(B), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if ((e = cudaMemcpyAsync(grad_queries, ctx->st_gq.p, 4 * total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (path && (e = cudaMemcpyAsync(path, ctx->st_path.p, 8 * total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(ctx, e);
+    }
+    if ((e = cudaMemcpyAsync(grad_ref, ctx->st_gr.p, 4 * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e);
+    ctx->key.valid = false;
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
+                          int32_t B, int32_t N, void* cost, int64_t* end, void* stream, sdtw_plan* plan)
+{
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
+    if (s != SDTW_OK) return s;
+    if (B == 0) return SDTW_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool ragged = offsets != nullptr;
+    const bool ckpt = (ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
+    float best_ms = 1e30f;
+    int best_w = 0, best_p = 0;
+    const int Ws[] = {8, 16, 32};
+    const int Ps[] = {2, 4, 8, 16};
+    for (int W : Ws) {
+        if (ckpt && ctx->K % W != 0) continue;
+        for (int P : Ps) {
+            if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
+            FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
+            p.W = W;
+            p.P = P;
+            p.block = 32 * P;
+            p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P);
+            if (p.smem > kMaxSmem) continue;
+            if (p.persistent) {
+                int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem);
+                if (per_sm <= 0) continue;
+                p.grid = std::max(1, std::min(B, per_sm * ctx->sm_count));
+            } else {
+                if (sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem) <= 0) continue;
+                p.grid = B;
+            }
+            // one untimed run, then the best of two timed runs
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, nullptr, 0, B);
+                cudaEventRecord(e1, st);
+                if (s != SDTW_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    s = SDTW_E_CUDA;
+                    break;
+                }
+                float t = 0;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);
+            }
+            if (s == SDTW_E_UNSUPPORTED) {
+                s = SDTW_OK;
+                continue;
+            }
+            if (s != SDTW_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return s;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_w = W;
+                best_p = P;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_w == 0) return SDTW_E_UNSUPPORTED;
+    ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] = {best_w, best_p};
+    ctx->key.valid = false;
+    if (plan) return sdtw_get_plan(ctx, B, N, M, ragged ? 1 : 0, 0, plan);
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_t ragged, int32_t backward,
+                          sdtw_plan* plan)
+{
+    if (!ctx || !plan || B < 1 || N < 1 || M < 1) return SDTW_E_INVALID;
+    const bool ckpt = backward || ((ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk);
+    if (backward && !(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    FwdPlan p = default_fwd_plan(ctx, backward ? std::min(B, ctx->bwd_chunk) : B, N, M, ragged != 0, ckpt);
+    std::memset(plan, 0, sizeof(*plan));
+    plan->seg_width = p.W;
+    plan->warps_per_query = p.P;
+    plan->ctas_per_query = 1;
+    plan->persistent = p.persistent ? 1 : 0;
+    plan->grid = p.persistent ? p.grid : B;
+    plan->block = p.block;
+    plan->smem_bytes = p.smem;
+    plan->ckpt_stride = ckpt ? ctx->K : 0;
+    plan->tuned = ctx->tuned.count(TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0})
+                      ? 1
+                      : 0;
+    plan->sweep_cols = static_cast<int64_t>(32) * p.P * p.W;
+    return SDTW_OK;
+}
+
+sdtw_status sdtw_last_device_status(sdtw_ctx* ctx, void* stream)
+{
+    if (!ctx) return SDTW_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    int v = 0;
+    if ((e = cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(ctx, e);
+    if (v != 0 && (e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(ctx, e);
+    if (v & sdtw::kStatusTimeout) return SDTW_E_TIMEOUT;
+    if (v) return SDTW_E_INVALID;
+    return SDTW_OK;
+}
+
+const char* sdtw_last_error(sdtw_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+size_t sdtw_workspace_bytes(sdtw_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+}  // extern "C"

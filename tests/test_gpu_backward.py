@@ -1,0 +1,210 @@
+"""GPU backward (walk-back gradient) against the CPU oracle, through the C ABI.
+
+What is unique is compared exactly: where the oracle's walk-back meets no
+near-tie (every step's best neighbour beats the runner-up by more than FP32
+can blur), the GPU path must be the oracle's path and its gradients must match
+the oracle's path gradient.  Where several paths are optimal within FP32
+resolution, the GPU path must be valid, its FP64 cost must equal the optimum
+within the cost tolerance, and the GPU gradients must equal the FP64 path
+gradient of the GPU's own path.  grad_ref must be the sum of the per-query
+path gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+from paper_2403_06931_gb300 import capi, inputs
+from paper_2403_06931_gb300.sdtw import SdtwContext, sdtw_cost
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 1e-4   # gradients: |g - o| <= GTOL * max|o| + 1e-6
+
+
+def run_bwd(dev, w, grad_cost=None, keep=True, **kw):
+    ref = torch.from_numpy(w.ref).to(dev)
+    qs = torch.from_numpy(w.queries).to(dev)
+    offs = torch.from_numpy(w.offsets).to(dev) if w.offsets is not None else None
+    N = int(w.lengths.max())
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=N, max_total_query_len=qs.numel(),
+                      grad=True, keep_checkpoints=keep, **kw)
+    cost, end = ctx.forward(ref, qs, offsets=offs, N=N if offs is not None else None)
+    g = torch.from_numpy(np.asarray(grad_cost, dtype=np.float32)).to(dev) if grad_cost is not None \
+        else torch.ones(w.B, device=dev)
+    gq, gr, path = ctx.backward(ref, qs, end, g, offsets=offs, N=N if offs is not None else None, want_path=True)
+    assert ctx.device_status() == capi.SDTW_OK
+    ctx.close()
+    return (cost.cpu().numpy(), end.cpu().numpy(), gq.cpu().numpy(), gr.cpu().numpy(),
+            path.cpu().numpy().reshape(-1, 2), g.cpu().numpy())
+
+
+def _rows(w, path, q):
+    a = w.offsets[q] if w.offsets is not None else q * w.N
+    n = int(w.lengths[q])
+    return path[a:a + n, 0], path[a:a + n, 1]
+
+
+def _gq(w, gq, q):
+    if w.offsets is not None:
+        return gq[w.offsets[q]:w.offsets[q + 1]]
+    return gq[q]
+
+
+def check_validity(w, cost, end, gq, gr, path, g, idx, oracle_costs):
+    """Path valid and optimal; gradients equal the FP64 gradient of the GPU's path."""
+    y = w.ref.astype(np.float64)
+    gy_sum = np.zeros(w.M)
+    for k, q in enumerate(idx):
+        x = w.query(q).astype(np.float64)
+        lo, hi = _rows(w, path, q)
+        assert oracle.intervals_are_valid(lo, hi, w.M, int(end[q])), q
+        pc = oracle.intervals_cost(x, y, lo, hi)
+        oc = oracle_costs[k]
+        assert abs(pc - oc) <= parity.cost_tol(oc, len(x)), (q, pc, oc)
+        gx, gyq = oracle.intervals_gradient(x, y, lo, hi, g=float(g[q]))
+        scale = max(np.abs(gx).max(), 1e-12)
+        assert np.all(np.abs(_gq(w, gq, q) - gx) <= GTOL * scale + 1e-6), q
+        gy_sum += gyq
+    return gy_sum
+
+
+def test_grad_subset_matches_oracle_paths(gpu):
+    """8 x 64 vs 512: exact path agreement away from near-ties, and gradients."""
+    w = inputs.grad_subset()
+    g = np.linspace(0.5, 2.0, w.B)
+    cost, end, gq, gr, path, gd = run_bwd(gpu, w, grad_cost=g)
+    y = w.ref.astype(np.float64)
+    oc, oe = oracle.forward_batch(w.ref, w.queries)
+    gy_sum = check_validity(w, cost, end, gq, gr, path, gd, range(w.B), oc)
+    assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
+    exact = 0
+    for q in range(w.B):
+        x = w.query(q).astype(np.float64)
+        cells, margins = oracle.walkback(x, y, int(oe[q]))
+        near_tie = (margins[margins >= 0] <= 1e-4 * oc[q] + 1e-5).any()
+        if near_tie or int(end[q]) != int(oe[q]):
+            continue
+        lo, hi = oracle.intervals_from_cells(cells, len(x))
+        glo, ghi = _rows(w, path, q)
+        assert np.array_equal(glo, lo) and np.array_equal(ghi, hi), q
+        gx, _ = oracle.path_gradient(x, y, cells, g=float(gd[q]))
+        assert np.all(np.abs(gq[q] - gx) <= GTOL * np.abs(gx).max() + 1e-6)
+        exact += 1
+    assert exact >= 4
+
+
+@pytest.mark.parametrize("B,N,M,K", [(4, 50, 700, 64), (3, 300, 2000, 128), (2, 129, 5000, 256),
+                                     (3, 1, 300, 64), (2, 40, 1, 64), (2, 700, 600, 128)])
+def test_backward_shapes(gpu, B, N, M, K):
+    w = inputs.tiny(B=B, N=N, M=M, seed=500 + B + N + M)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=K)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    gy_sum = check_validity(w, cost, end, gq, gr, path, g, range(B), oc)
+    assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
+
+
+def test_backward_long_vertical_runs_cross_windows(gpu):
+    # a query far longer than the reference forces long vertical runs, so the
+    # walk climbs many rows inside one block (several direction-code windows)
+    w = inputs.tiny(B=2, N=2500, M=300, seed=61)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+
+
+def test_backward_ragged(gpu):
+    w = inputs.ragged_fp32(B=7, n_lo=1, n_hi=300, M=2500, seed=71)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w)
+    oc, _ = oracle.forward_batch(w.ref, w.queries, offsets=w.offsets)
+    gy_sum = check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+    assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
+
+
+def test_chunked_and_recomputed_backward_are_identical(gpu):
+    w = inputs.tiny(B=9, N=200, M=4000, seed=81)
+    a = run_bwd(gpu, w, keep=True)                          # checkpoints from the forward
+    b = run_bwd(gpu, w, keep=False)                         # backward re-runs the forward
+    per_q = 4 * 200 * (4000 // 64) + 4 * 4000 + 32
+    c = run_bwd(gpu, w, keep=False, mem_cap_bytes=3 * per_q + 200_000)   # forces chunks of queries
+    for u, v in ((a, b), (a, c)):
+        for k in range(5):
+            assert np.array_equal(u[k], v[k])
+
+
+def test_host_forward_backward_matches_device(gpu):
+    w = inputs.tiny(B=5, N=120, M=2000, seed=91)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True, keep_checkpoints=True)
+    hc = np.empty(w.B, np.float32)
+    he = np.empty(w.B, np.int64)
+    hgq = np.empty_like(w.queries)
+    hgr = np.empty_like(w.ref)
+    hp = np.empty(w.queries.size * 2, np.int32)
+    gc = np.ones(w.B, np.float32)
+    st = capi.sdtw_forward_backward_host(ctx.handle, w.ref.ctypes.data, w.M, w.queries.ctypes.data, None, w.B,
+                                         w.N, gc.ctypes.data, hc.ctypes.data, he.ctypes.data, hgq.ctypes.data,
+                                         hgr.ctypes.data, hp.ctypes.data, None)
+    assert st == capi.SDTW_OK
+    assert np.array_equal(hc, cost) and np.array_equal(he, end) and np.array_equal(hgq, gq)
+    assert np.array_equal(hgr, gr) and np.array_equal(hp.reshape(-1, 2), path)
+    ctx.close()
+
+
+def test_autograd_function(gpu):
+    w = inputs.tiny(B=4, N=60, M=900, seed=93)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True, keep_checkpoints=True)
+    ref = torch.from_numpy(w.ref).to(gpu).requires_grad_(True)
+    qs = torch.from_numpy(w.queries).to(gpu).requires_grad_(True)
+    cost, end = sdtw_cost(ref, qs, ctx)
+    wts = torch.tensor([1.0, -0.5, 2.0, 0.25], device=gpu)
+    (cost * wts).sum().backward()
+    gq, gr, _ = ctx.backward(ref.detach(), qs.detach(), end, wts)
+    assert torch.equal(qs.grad, gq) and torch.equal(ref.grad, gr)
+    ctx.close()
+
+
+def test_backward_rejections(gpu):
+    ctx = SdtwContext(dtype="i8", max_ref_len=100, max_batch=2, max_query_len=10)
+    z = torch.zeros(100, dtype=torch.int8, device=gpu)
+    st = capi.sdtw_backward(ctx.handle, z.data_ptr(), 100, z.data_ptr(), None, 2, 10, z.data_ptr(),
+                            z.data_ptr(), z.data_ptr(), z.data_ptr(), None, None)
+    assert st == capi.SDTW_E_UNSUPPORTED
+    ctx.close()
+    ctx = SdtwContext(max_ref_len=100, max_batch=2, max_query_len=10)       # no grad flag
+    f = torch.zeros(100, device=gpu)
+    st = capi.sdtw_backward(ctx.handle, f.data_ptr(), 100, f.data_ptr(), None, 2, 10, f.data_ptr(),
+                            f.data_ptr(), f.data_ptr(), f.data_ptr(), None, None)
+    assert st == capi.SDTW_E_INVALID
+    ctx.close()
+
+
+def test_backward_bad_end_is_flagged(gpu):
+    w = inputs.tiny(B=2, N=20, M=300, seed=95)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    end = torch.tensor([5, 300], dtype=torch.int64, device=gpu)     # 300 is outside [0, M)
+    ctx.backward(ref, qs, end, torch.ones(2, device=gpu))
+    assert ctx.device_status() == capi.SDTW_E_INVALID
+    ctx.close()
+
+
+def test_paper_batch_backward_full_size(gpu):
+    """512 x 2,000 vs 100,000 with checkpoints kept by the forward (the bench's
+    configuration): every path valid; 12 sampled queries checked against the
+    oracle's cost and their gradients; grad_ref equals the sum of path gradients."""
+    w = inputs.paper_fp32()
+    cost, end, gq, gr, path, g = run_bwd(gpu, w)
+    y = w.ref.astype(np.float64)
+    gy_all = np.zeros(w.M)
+    for q in range(w.B):
+        lo, hi = _rows(w, path, q)
+        assert oracle.intervals_are_valid(lo, hi, w.M, int(end[q])), q
+        _, gyq = oracle.intervals_gradient(w.query(q).astype(np.float64), y, lo, hi, g=1.0)
+        gy_all += gyq
+    assert np.all(np.abs(gr - gy_all) <= GTOL * np.abs(gy_all).max() + 1e-5)
+    idx = sorted(np.random.default_rng(5).choice(w.B, size=12, replace=False).tolist())
+    oc, _ = oracle.forward_batch(w.ref, w.queries, indices=idx)
+    check_validity(w, cost, end, gq, gr, path, g, idx, oc)

@@ -296,3 +296,32 @@ def test_oracle_rejects_bad_sizes(oracle_mod):
         oracle_mod.forward(np.zeros(0), np.zeros(4))
     with pytest.raises(ValueError):
         oracle_mod.walkback(np.zeros(3), np.zeros(4), 4)
+
+
+# ------------------------------------------------------- interval form --
+
+def test_interval_helpers_agree_with_cell_helpers(oracle_mod):
+    w = inputs.tiny(B=5, N=30, M=400, seed=31)
+    y = w.ref.astype(np.float64)
+    for q in range(w.B):
+        x = w.query(q).astype(np.float64)
+        c, e = oracle_mod.forward(x, y)
+        cells, _ = oracle_mod.walkback(x, y, e)
+        lo, hi = oracle_mod.intervals_from_cells(cells, len(x))
+        assert oracle_mod.intervals_are_valid(lo, hi, len(y), e)
+        assert math.isclose(oracle_mod.intervals_cost(x, y, lo, hi), oracle_mod.path_cost(x, y, cells),
+                            rel_tol=1e-11)
+        gx, gy = oracle_mod.intervals_gradient(x, y, lo, hi, g=0.7)
+        hx, hy = oracle_mod.path_gradient(x, y, cells, g=0.7)
+        np.testing.assert_allclose(gx, hx, rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(gy, hy, rtol=1e-10, atol=1e-10)
+
+
+def test_interval_validity_rejects_bad_runs(oracle_mod):
+    assert oracle_mod.intervals_are_valid([1, 2, 4], [1, 3, 4], 5, 4)
+    assert not oracle_mod.intervals_are_valid([1, 2, 4], [1, 3, 4], 5, 3)   # wrong end
+    assert not oracle_mod.intervals_are_valid([1, 3, 4], [1, 3, 4], 5, 4)   # jump of two columns
+    assert oracle_mod.intervals_are_valid([1, 2, 3], [1, 3, 4], 5, 4)       # up step from (2,3) to (1,3)
+    assert not oracle_mod.intervals_are_valid([1, 2, 2], [1, 3, 4], 5, 4)   # run overlaps previous row
+    assert not oracle_mod.intervals_are_valid([1, 2, 4], [1, 1, 4], 5, 4)   # lo > hi
+    assert not oracle_mod.intervals_are_valid([1, 2, 4], [1, 3, 5], 5, 5)   # outside the matrix
