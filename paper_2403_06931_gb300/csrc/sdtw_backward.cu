@@ -10,8 +10,8 @@
 // The n x M matrix is never stored.  The forward pass left one DP column every
 // K columns (its checkpoints).  The walk proceeds right to left through blocks
 // of K columns: for the block holding the current cell (i, j) one warp
-// recomputes rows 0..i from the checkpoint column on its left (the same FP32
-// operations as the forward, so the values are bit-identical), records for each
+// recomputes rows 0..i from the checkpoint column on its left (FP32 relative to
+// per-lane bases, rebased every kChunk rows as in the forward), records for each
 // cell which neighbour the walk-back would take (two bits), and lane 0 then
 // walks the path through the block, accumulating the gradient.  Direction codes
 // are kept for a window of kWin rows; a path that climbs above the window
@@ -131,20 +131,35 @@ __global__ void __launch_bounds__(32) bwd_walk_kernel(const BwdArgs a)
             D[k] = 0.f;
         }
         float diag = 0.f;
+        float B = 0.f;  // per-lane base, as in the forward: absolute D = B + D'
         const int steps = rows + 31;
         for (int t = 0; t < steps; ++t) {
+            if ((t & (kChunk - 1)) == 0) {
+                const float bn = floorf(B + D[0]);
+                const float dl = bn - B;
+#pragma unroll
+                for (int k = 0; k < WB; ++k) D[k] -= dl;
+                diag -= dl;
+                B = bn;
+            }
             float recv = __shfl_up_sync(0xffffffffu, D[WB - 1], 1);
+            float rb = __shfl_up_sync(0xffffffffu, B, 1);
             const int r = t - lane;
             const bool act = static_cast<unsigned>(r) < static_cast<unsigned>(rows);
-            if (lane == 0) recv = (act && b > 0) ? bcol[r] : INF;
+            if (lane == 0) {
+                recv = (act && b > 0) ? bcol[r] : INF;  // checkpoints hold absolute values
+                rb = 0.f;
+            }
             if (act) {
                 if (r == 0) {
 #pragma unroll
                     for (int k = 0; k < WB; ++k) D[k] = 0.f;
                     diag = 0.f;
+                    B = 0.f;
                 }
                 const float xv = xs[r];
-                float left = recv;
+                float left = recv + (rb - B);
+                const float conv = left;
                 uint32_t code = 0;
 #pragma unroll
                 for (int k = 0; k < WB; ++k) {
@@ -161,7 +176,7 @@ __global__ void __launch_bounds__(32) bwd_walk_kernel(const BwdArgs a)
                     left = nv;
                     D[k] = nv;
                 }
-                diag = recv;
+                diag = conv;
                 if (r >= win_lo) dirs[(r - win_lo) * 32 + lane] = static_cast<DW>(code);
             }
         }

@@ -29,6 +29,8 @@ struct Mode;
 template <>
 struct Mode<float> {
     using V = float;  // x, y and D
+    // FP32 D values are kept relative to a per-thread base (see sdtw_forward.cu)
+    static constexpr bool kRebase = true;
     static __device__ __forceinline__ V inf() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ V empty_cost() { return inf(); }  // empty query
     static __device__ __forceinline__ V zero() { return 0.0f; }
@@ -43,6 +45,7 @@ struct Mode<float> {
 template <>
 struct Mode<int8_t> {
     using V = int32_t;
+    static constexpr bool kRebase = false;  // integer sums are exact
     // Largest finite float pattern: above every reachable cost (N <= 33,000
     // samples of at most 254^2 each), and never NaN or infinity.
     static __device__ __forceinline__ V inf() { return 0x7f7fffff; }

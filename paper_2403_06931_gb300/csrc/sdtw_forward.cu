@@ -28,8 +28,21 @@
 // a strict '<' in increasing column order, then reduced over the CTA
 // lexicographically, so the smallest end column wins exact ties.
 //
+// FP32 accuracy.  D grows along the query (to ~10^3 for N = 2,000), so one
+// rounding of an FP32 cell costs ~10^-4 absolute, and the minimum over near-tied
+// neighbours systematically keeps the one that rounded low: over a 2,000-row
+// path plain FP32 drifts 3e-6 low on average and up to ~1.4e-5 (relative).  In
+// FP32 mode each thread therefore stores its strip relative to a base B of its
+// own (D = B + D'), and every kChunk steps all threads rebase to the integer
+// part of their strip's first column, so the stored D' stay small; integer
+// bases make every base difference exact, so exact costs (e.g. 0 for an exact
+// cut of the reference) stay exact.
+// Values crossing threads travel with their sender's base and are converted
+// on receipt; a sweep starts from base 0.  The drift falls below 1e-7 and the
+// worst error to ~1.5e-6, for one shuffle and two adds per step (W cells).
+//
 // Optional checkpoints for the backward pass: a thread whose strip ends at a
-// multiple of K stores that column's D value for every row.
+// multiple of K stores that column's absolute D value for every row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,9 +75,11 @@ fwd_chain_kernel(const FwdArgs a)
     const int nsw = (M + S - 1) / S;
 
     V* xs = reinterpret_cast<V*>(smem_raw);               // [N]   query samples
-    V* colbuf = xs + N;                                    // [N]   sweep boundary column
-    V* ring = colbuf + N;                                  // [P][kRing] warp-to-warp ring
-    V* red_v = ring + P * kRing;                           // [P]   reduction scratch
+    V* colv = xs + N;                                      // [N]   sweep boundary column (values)
+    float* colb = reinterpret_cast<float*>(colv + N);      // [N]   ... and their bases
+    V* ringv = reinterpret_cast<V*>(colb + N);             // [P][kRing] warp-to-warp ring (values)
+    float* ringb = reinterpret_cast<float*>(ringv + P * kRing);  // [P][kRing] ... and bases
+    V* red_v = reinterpret_cast<V*>(ringb + P * kRing);    // [P]   reduction scratch
     int* red_i = reinterpret_cast<int*>(red_v + P);        // [P]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
@@ -73,8 +88,10 @@ fwd_chain_kernel(const FwdArgs a)
     const int64_t first_start = a.offsets ? a.offsets[a.q0] : static_cast<int64_t>(a.q0) * a.N;
     const int lag = warp * (32 + kChunk) + lane;
     const int lag_last = (P - 1) * (32 + kChunk) + 31;
-    const V* ring_in = ring + warp * kRing;
-    V* ring_out = ring + (warp + 1) * kRing;
+    const V* ringv_in = ringv + warp * kRing;
+    const float* ringb_in = ringb + warp * kRing;
+    V* ringv_out = ringv + (warp + 1) * kRing;
+    float* ringb_out = ringb + (warp + 1) * kRing;
 
     for (int it = 0;; ++it) {
         int q;
@@ -130,6 +147,7 @@ fwd_chain_kernel(const FwdArgs a)
             D[k] = Md::zero();
         }
         V diag = Md::zero();
+        float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
         V best = Md::inf();
         int best_col = INT_MAX;
         int r = -lag;  // query row of this thread's strip (negative: not started)
@@ -138,16 +156,35 @@ fwd_chain_kernel(const FwdArgs a)
         float* ck = nullptr;
 
         for (int t0 = 0; t0 < total; t0 += kChunk) {
-#pragma unroll 2
+            if constexpr (Md::kRebase) {
+                // new base: the integer part of the strip's first column; bases
+                // are integers (exact below 2^24), so base differences, the
+                // shift and every conversion between threads add no rounding
+                const float bn = floorf(B + D[0]);
+                const float dl = bn - B;
+#pragma unroll
+                for (int k = 0; k < W; ++k) D[k] -= dl;
+                diag -= dl;
+                B = bn;
+            }
+#pragma unroll 1
             for (int u = 0; u < kChunk; ++u) {
                 const int t = t0 + u;
                 V recv = __shfl_up_sync(0xffffffffu, D[W - 1], 1);
+                float rb = 0.f;
+                if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
                 const bool act = static_cast<unsigned>(r) < static_cast<unsigned>(n) && s < nsw;
                 if (lane == 0) {
                     if (warp > 0) {
-                        recv = ring_in[(t - kChunk - 1) & (kRing - 1)];
+                        const int slot = (t - kChunk - 1) & (kRing - 1);
+                        recv = ringv_in[slot];
+                        if constexpr (Md::kRebase) rb = ringb_in[slot];
+                    } else if (act && s > 0) {
+                        recv = colv[r];
+                        if constexpr (Md::kRebase) rb = colb[r];
                     } else {
-                        recv = (act && s > 0) ? colbuf[r] : Md::inf();
+                        recv = Md::inf();
+                        rb = 0.f;
                     }
                 }
                 if (act) {
@@ -162,6 +199,7 @@ fwd_chain_kernel(const FwdArgs a)
                             D[k] = Md::zero();
                         }
                         diag = Md::zero();
+                        B = 0.f;
                         ck = nullptr;
                         if (a.ckpt) {
                             const int edge = base + W;
@@ -169,8 +207,10 @@ fwd_chain_kernel(const FwdArgs a)
                                 ck = a.ckpt + (start - first_start) * a.nblk + static_cast<int64_t>(edge / a.K - 1) * n;
                         }
                     }
-                    const V xv = xs[r];
                     V left = recv;
+                    if constexpr (Md::kRebase) left = recv + (rb - B);  // into this thread's base
+                    const V conv = left;
+                    const V xv = xs[r];
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         const V up = D[k];
@@ -179,23 +219,28 @@ fwd_chain_kernel(const FwdArgs a)
                         left = nv;
                         D[k] = nv;
                     }
-                    diag = recv;
+                    diag = conv;
                     if (r == n - 1) {
 #pragma unroll
                         for (int k = 0; k < W; ++k) {
-                            if (base + k < M && D[k] < best) {
-                                best = D[k];
+                            V v = D[k];
+                            if constexpr (Md::kRebase) v = B + D[k];
+                            if (base + k < M && v < best) {
+                                best = v;
                                 best_col = base + k;
                             }
                         }
                     }
                     if (lane == 31) {
-                        if (warp < P - 1)
-                            ring_out[t & (kRing - 1)] = D[W - 1];
-                        else
-                            colbuf[r] = D[W - 1];
+                        if (warp < P - 1) {
+                            ringv_out[t & (kRing - 1)] = D[W - 1];
+                            if constexpr (Md::kRebase) ringb_out[t & (kRing - 1)] = B;
+                        } else {
+                            colv[r] = D[W - 1];
+                            if constexpr (Md::kRebase) colb[r] = B;
+                        }
                     }
-                    if (ck) ck[r] = static_cast<float>(D[W - 1]);
+                    if (ck) ck[r] = static_cast<float>(D[W - 1]) + B;
                 }
                 if (++r == Np) {
                     r = 0;
@@ -301,8 +346,9 @@ bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 3
 
 int fwd_smem_bytes(sdtw_dtype, int N, int P)
 {
-    // xs[N] + colbuf[N] + ring[P][kRing] + reduction (value, index)[P]; 4-byte elements
-    return 4 * (2 * N + P * kRing + 2 * P);
+    // xs[N] + column values and bases [2N] + ring values and bases [2P*kRing]
+    // + reduction (value, index)[P]; 4-byte elements
+    return 4 * (3 * N + 2 * P * kRing + 2 * P);
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P)

@@ -1,0 +1,73 @@
+"""Run the library on one seeded workload from the command line.
+
+    python -m paper_2403_06931_gb300.run_case --workload paper --B 152 --reps 3 [--backward] [--dtype i8]
+
+Used to profile a single kernel on a chosen shape (e.g. under ncu) and as a
+quick end-to-end check: prints the plan, the mean kernel time and GCUPS.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import inputs
+from .sdtw import SdtwContext
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="paper", choices=["paper", "ragged", "small", "grad"])
+    ap.add_argument("--B", type=int, default=None, help="queries (default: the workload's)")
+    ap.add_argument("--N", type=int, default=None)
+    ap.add_argument("--M", type=int, default=None)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i8"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--backward", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--seg-width", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    a = ap.parse_args()
+
+    kw = {k: v for k, v in (("B", a.B), ("N", a.N), ("M", a.M)) if v is not None}
+    if a.workload == "ragged":
+        kw = {k: v for k, v in (("B", a.B), ("M", a.M)) if v is not None}
+        w = inputs.ragged_fp32(**kw)
+    elif a.workload == "paper":
+        w = inputs.paper_i8(**kw) if a.dtype == "i8" else inputs.paper_fp32(**kw)
+    else:
+        w = inputs.by_name(a.workload)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ref = torch.from_numpy(w.ref).to(dev)
+    qs = torch.from_numpy(w.queries).to(dev)
+    offs = torch.from_numpy(w.offsets).to(dev) if w.offsets is not None else None
+    N = int(w.lengths.max())
+    ctx = SdtwContext(dtype=a.dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=N,
+                      max_total_query_len=qs.numel(), grad=a.backward, keep_checkpoints=a.backward,
+                      seg_width=a.seg_width, warps_per_query=a.warps)
+    if a.autotune:
+        ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
+    Nr = N if offs is not None else None
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cost, end = ctx.forward(ref, qs, offsets=offs, N=Nr)
+        if a.backward:
+            ctx.backward(ref, qs, end, torch.ones(w.B, device=dev), offsets=offs, N=Nr)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    status = ctx.device_status()
+    ms = sum(times) / len(times)
+    print(json.dumps({"workload": w.name, "B": w.B, "N": N, "M": w.M, "dtype": a.dtype, "backward": a.backward,
+                      "plan": ctx.plan(w.B, N, w.M, ragged=offs is not None), "ms": round(ms, 3),
+                      "gcups": round(w.cells / (ms * 1e-3) / 1e9, 2), "device_status": status}))
+    ctx.close()
+    if status != 0:
+        raise SystemExit(f"device status {status}")
+
+
+if __name__ == "__main__":
+    main()

@@ -83,7 +83,9 @@ def test_grad_subset_matches_oracle_paths(gpu):
     for q in range(w.B):
         x = w.query(q).astype(np.float64)
         cells, margins = oracle.walkback(x, y, int(oe[q]))
-        near_tie = (margins[margins >= 0] <= 1e-4 * oc[q] + 1e-5).any()
+        # a step whose best and second-best neighbours differ by less than 20x the
+        # FP32 error of D (about 1e-6 relative with per-lane rebasing) may go either way
+        near_tie = (margins[margins >= 0] <= 2e-5 * oc[q] + 1e-6 * len(x)).any()
         if near_tie or int(end[q]) != int(oe[q]):
             continue
         lo, hi = oracle.intervals_from_cells(cells, len(x))
