@@ -556,8 +556,8 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
     float best_ms = 1e30f;
     int best_w = 0, best_p = 0;
-    const int Ws[] = {8, 16, 32};
-    const int Ps[] = {2, 4, 8, 16};
+    const int Ws[] = {8, 12, 16, 24, 32};
+    const int Ps[] = {1, 2, 4, 8, 16};
     for (int W : Ws) {
         if (ckpt && ctx->K % W != 0) continue;
         for (int P : Ps) {

@@ -6,22 +6,27 @@
 //
 // Schedule.  The CTA's L = 32*P threads form a chain; thread l owns a strip of
 // W consecutive reference columns (the paper's "segment", Section 5.2) and
-// keeps the strip's current DP row and reference samples in registers.  At
-// every step a thread advances its strip by one query row, and thread l runs
-// one row behind thread l-1, so one step fills an anti-diagonal of strips.
-// The strip's right-hand cell travels to the next thread by __shfl_up_sync
-// inside a warp; between warps it goes through a small shared-memory ring,
-// and warp w runs kChunk+1 steps further behind warp w-1 so that one CTA
-// barrier every kChunk steps orders every ring write before its read.
+// keeps the strip's reference samples and its latest DP row in registers.  At
+// every step a thread advances its strip by a pair of query rows (a 2 x W
+// register tile), and thread l runs one step behind thread l-1, so one step
+// fills an anti-diagonal of tiles.  Inside the tile, cells (r, k) and
+// (r+1, k-1) are independent, so each thread runs two dependency chains; row r
+// goes to a scratch strip and row r+1 overwrites the previous row one column
+// behind it, so no register has to be moved between steps.  The tile's two
+// right-hand cells travel to the next thread by __shfl_up_sync inside a warp;
+// between warps they go through a small shared-memory ring, and warp w runs
+// kChunk+1 steps further behind warp w-1 so that one CTA barrier every kChunk
+// steps orders every ring write before its read.
 //
 // The chain covers S = L*W columns per sweep.  Sweeps are continuous: when a
-// thread finishes the last query row of sweep s it starts row 0 of sweep s+1
-// (columns shifted by S) on the next step, and the chain's last thread leaves
-// the sweep's right-hand column in a shared-memory column buffer that the
-// first thread reads one sweep later (the paper's double-buffered column
-// between wavefronts, Section 5.2, kept as a single buffer indexed by row).
-// Threads therefore never idle between sweeps; only the chain's start and end
-// are ragged.
+// thread finishes the last row pair of sweep s it starts row pair 0 of sweep
+// s+1 (columns shifted by S) on the next step, and the chain's last thread
+// leaves the sweep's right-hand column in a shared-memory column buffer that
+// the first thread reads one sweep later (the paper's double-buffered column
+// between wavefronts, Section 5.2, kept as one buffer indexed by row pair).
+// Threads never idle between sweeps; only the chain's start and end are
+// ragged.  Chunks in which no thread of a warp starts a sweep or reaches the
+// bottom row run a fast path without per-step bookkeeping.
 //
 // The bottom-row minimum (Section 5.2 aggregates it while the last row is
 // produced) is kept per thread as a running (value, column) pair updated with
@@ -36,10 +41,9 @@
 // own (D = B + D'), and every kChunk steps all threads rebase to the integer
 // part of their strip's first column, so the stored D' stay small; integer
 // bases make every base difference exact, so exact costs (e.g. 0 for an exact
-// cut of the reference) stay exact.
-// Values crossing threads travel with their sender's base and are converted
-// on receipt; a sweep starts from base 0.  The drift falls below 1e-7 and the
-// worst error to ~1.5e-6, for one shuffle and two adds per step (W cells).
+// cut of the reference) stay exact.  Values crossing threads travel with their
+// sender's base and are converted on receipt; a sweep starts from base 0.  The
+// drift falls below 1e-7 and the worst error to ~1.5e-6.
 //
 // Optional checkpoints for the backward pass: a thread whose strip ends at a
 // multiple of K stores that column's absolute D value for every row.
@@ -55,12 +59,65 @@
 namespace sdtw {
 namespace {
 
+// The two right-hand cells of one row pair of a strip, with their base.
+template <typename V>
+struct alignas(16) Edge {
+    V v0, v1;
+    float b;
+    int pad;
+};
+
+template <typename V>
+struct Pair2;
+template <>
+struct Pair2<float> { using T = float2; };
+template <>
+struct Pair2<int32_t> { using T = int2; };
+
+// One 2 x W tile: rows r (into A) and r+1 (over prev), walking the
+// anti-diagonals of the tile so that the two rows form independent chains.
+//   prev   in: row r-1 of the strip; out: row r+1
+//   A      out: row r (A[W-1] is kept for the next step's send)
+//   diag   D(r-1, c-1);  left0 = D(r, c-1);  left1 = D(r+1, c-1)
+template <typename Md, int W>
+__device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md::V (&A)[W],
+                                          const typename Md::V (&y)[W], typename Md::V x0,
+                                          typename Md::V x1, typename Md::V diag,
+                                          typename Md::V left0, typename Md::V left1)
+{
+    using V = typename Md::V;
+#pragma unroll
+    for (int k = 0; k <= W; ++k) {
+        if (k < W) {
+            const V up = prev[k];
+            const V dg = k == 0 ? diag : prev[k - 1];
+            const V lf = k == 0 ? left0 : A[k - 1];
+            A[k] = Md::cell(x0, y[k], up, dg, lf);
+        }
+        if (k >= 1) {
+            const int j = k - 1;
+            const V up = A[j];
+            const V dg = j == 0 ? left0 : A[j - 1];
+            const V lf = j == 0 ? left1 : prev[j - 1];
+            prev[j] = Md::cell(x1, y[j], up, dg, lf);
+        }
+    }
+}
+
+// Register cap per segment width: the strip's samples and previous row (2W)
+// plus the tile's short-lived values and bookkeeping, leaving room for several
+// CTAs per SM.
+template <int W>
+constexpr int fwd_reg_cap() { return W <= 8 ? 72 : W <= 12 ? 80 : W <= 16 ? 88 : W <= 24 ? 112 : 128; }
+
 template <typename Tin, int W>
-__global__ void __launch_bounds__(kMaxWarpsPerQuery * 32)
+__global__ void __maxnreg__(fwd_reg_cap<W>())
 fwd_chain_kernel(const FwdArgs a)
 {
     using Md = Mode<Tin>;
     using V = typename Md::V;
+    using E = Edge<V>;
+    using V2 = typename Pair2<V>::T;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_query;
@@ -68,30 +125,28 @@ fwd_chain_kernel(const FwdArgs a)
     const int P = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int L = blockDim.x;
     const int N = a.N;
+    const int Npad = (N + 1) & ~1;
     const int M = static_cast<int>(a.M);
-    const int S = L * W;
+    const int S = blockDim.x * W;
     const int nsw = (M + S - 1) / S;
 
-    V* xs = reinterpret_cast<V*>(smem_raw);               // [N]   query samples
-    V* colv = xs + N;                                      // [N]   sweep boundary column (values)
-    float* colb = reinterpret_cast<float*>(colv + N);      // [N]   ... and their bases
-    V* ringv = reinterpret_cast<V*>(colb + N);             // [P][kRing] warp-to-warp ring (values)
-    float* ringb = reinterpret_cast<float*>(ringv + P * kRing);  // [P][kRing] ... and bases
-    V* red_v = reinterpret_cast<V*>(ringb + P * kRing);    // [P]   reduction scratch
+    E* ring = reinterpret_cast<E*>(smem_raw);              // [P][kRing] warp-to-warp ring
+    E* colbuf = ring + P * kRing;                          // [Npad/2]  sweep boundary column
+    V* xs = reinterpret_cast<V*>(colbuf + Npad / 2);       // [Npad]    query samples (zero padded)
+    V* red_v = xs + Npad;                                  // [P]       reduction scratch
     int* red_i = reinterpret_cast<int*>(red_v + P);        // [P]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
 
     const int64_t first_start = a.offsets ? a.offsets[a.q0] : static_cast<int64_t>(a.q0) * a.N;
-    const int lag = warp * (32 + kChunk) + lane;
+    const int wlag = warp * (32 + kChunk);
+    const int lag = wlag + lane;
     const int lag_last = (P - 1) * (32 + kChunk) + 31;
-    const V* ringv_in = ringv + warp * kRing;
-    const float* ringb_in = ringb + warp * kRing;
-    V* ringv_out = ringv + (warp + 1) * kRing;
-    float* ringb_out = ringb + (warp + 1) * kRing;
+    const E* ring_in = ring + warp * kRing;
+    E* ring_out = ring + (warp + 1) * kRing;
+    const V INF = Md::inf();
 
     for (int it = 0;; ++it) {
         int q;
@@ -135,23 +190,28 @@ fwd_chain_kernel(const FwdArgs a)
         }
 
         for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = Md::widen(queries[start + i]);
+        if (threadIdx.x == 0 && (n & 1)) xs[n] = Md::zero();  // a dummy row completes the last pair
         __syncthreads();
 
-        const int Np = max(n, lag_last + kChunk);
-        const int total = (nsw - 1) * Np + n + lag_last;
+        const int npairs = (n + 1) >> 1;
+        const int lastp = npairs - 1;                      // the pair holding row n-1
+        const int Pp = max(npairs, lag_last + kChunk);     // sweep period in steps
+        const int total = (nsw - 1) * Pp + npairs + lag_last;
+        const V2* xs2 = reinterpret_cast<const V2*>(xs);
 
-        V y[W], D[W];
+        V y[W], prev[W], A[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             y[k] = Md::zero();
-            D[k] = Md::zero();
+            prev[k] = Md::zero();
+            A[k] = Md::zero();
         }
         V diag = Md::zero();
         float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
-        V best = Md::inf();
+        V best = INF;
         int best_col = INT_MAX;
-        int r = -lag;  // query row of this thread's strip (negative: not started)
-        int s = 0;     // sweep
+        int p = -lag;   // row pair of this thread's tile in sweep s (negative: not started)
+        int s = 0;      // sweep
         int base = threadIdx.x * W;  // first column of the strip in sweep s
         float* ck = nullptr;
 
@@ -160,91 +220,162 @@ fwd_chain_kernel(const FwdArgs a)
                 // new base: the integer part of the strip's first column; bases
                 // are integers (exact below 2^24), so base differences, the
                 // shift and every conversion between threads add no rounding
-                const float bn = floorf(B + D[0]);
+                const float bn = floorf(B + prev[0]);
                 const float dl = bn - B;
 #pragma unroll
-                for (int k = 0; k < W; ++k) D[k] -= dl;
+                for (int k = 0; k < W; ++k) prev[k] -= dl;
+                A[W - 1] -= dl;
                 diag -= dl;
                 B = bn;
             }
+            // fast path: no thread of this warp starts a sweep, idles or meets the
+            // bottom row during the chunk (the test is uniform over the warp)
+            const int gmin = t0 - wlag - 31;
+            const int gmax = t0 - wlag + kChunk - 1;
+            bool fast = gmin >= 0;
+            if (fast) {
+                const int sw = gmin / Pp;
+                fast = gmax / Pp == sw && sw < nsw && gmin - sw * Pp >= 1 && gmax - sw * Pp <= lastp - 1;
+            }
+            if (fast) {
+                float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
+                if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
 #pragma unroll 1
-            for (int u = 0; u < kChunk; ++u) {
-                const int t = t0 + u;
-                V recv = __shfl_up_sync(0xffffffffu, D[W - 1], 1);
-                float rb = 0.f;
-                if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
-                const bool act = static_cast<unsigned>(r) < static_cast<unsigned>(n) && s < nsw;
-                if (lane == 0) {
-                    if (warp > 0) {
-                        const int slot = (t - kChunk - 1) & (kRing - 1);
-                        recv = ringv_in[slot];
-                        if constexpr (Md::kRebase) rb = ringb_in[slot];
-                    } else if (act && s > 0) {
-                        recv = colv[r];
-                        if constexpr (Md::kRebase) rb = colb[r];
-                    } else {
-                        recv = Md::inf();
-                        rb = 0.f;
+                for (int u = 0; u < kChunk; ++u) {
+                    const int t = t0 + u;
+                    V v0 = __shfl_up_sync(0xffffffffu, A[W - 1], 1);
+                    V v1 = __shfl_up_sync(0xffffffffu, prev[W - 1], 1);
+                    float dd = dconv;
+                    if (lane == 0) {
+                        if (warp > 0) {
+                            const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
+                            v0 = e.v0;
+                            v1 = e.v1;
+                            dd = e.b - B;
+                        } else if (s > 0) {
+                            const E e = colbuf[p];
+                            v0 = e.v0;
+                            v1 = e.v1;
+                            dd = e.b - B;
+                        } else {
+                            v0 = INF;
+                            v1 = INF;
+                            dd = 0.f;
+                        }
                     }
+                    V left0 = v0, left1 = v1;
+                    if constexpr (Md::kRebase) {
+                        left0 = v0 + dd;
+                        left1 = v1 + dd;
+                    }
+                    const V2 xp = xs2[p];
+                    tile_step<Md, W>(prev, A, y, xp.x, xp.y, diag, left0, left1);
+                    diag = left1;
+                    if (lane == 31) {
+                        E e;
+                        e.v0 = A[W - 1];
+                        e.v1 = prev[W - 1];
+                        e.b = B;
+                        e.pad = 0;
+                        if (warp < P - 1)
+                            ring_out[t & (kRing - 1)] = e;
+                        else
+                            colbuf[p] = e;
+                    }
+                    if (ck) {
+                        ck[2 * p] = static_cast<float>(A[W - 1]) + B;
+                        ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
+                    }
+                    ++p;
                 }
-                if (act) {
-                    if (r == 0) {
-                        // new sweep: load the strip's reference samples; the
-                        // previous row is the virtual all-zero row -1
-                        base = s * S + threadIdx.x * W;
-#pragma unroll
-                        for (int k = 0; k < W; ++k) {
-                            const int col = base + k;
-                            y[k] = col < M ? Md::widen(ref[col]) : Md::zero();
-                            D[k] = Md::zero();
-                        }
-                        diag = Md::zero();
-                        B = 0.f;
-                        ck = nullptr;
-                        if (a.ckpt) {
-                            const int edge = base + W;
-                            if (edge % a.K == 0 && edge / a.K <= a.nblk)
-                                ck = a.ckpt + (start - first_start) * a.nblk + static_cast<int64_t>(edge / a.K - 1) * n;
+            } else {
+#pragma unroll 1
+                for (int u = 0; u < kChunk; ++u) {
+                    const int t = t0 + u;
+                    V v0 = __shfl_up_sync(0xffffffffu, A[W - 1], 1);
+                    V v1 = __shfl_up_sync(0xffffffffu, prev[W - 1], 1);
+                    float rb = 0.f;
+                    if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
+                    const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(npairs) && s < nsw;
+                    if (lane == 0) {
+                        if (warp > 0) {
+                            const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
+                            v0 = e.v0;
+                            v1 = e.v1;
+                            rb = e.b;
+                        } else if (act && s > 0) {
+                            const E e = colbuf[p];
+                            v0 = e.v0;
+                            v1 = e.v1;
+                            rb = e.b;
+                        } else {
+                            v0 = INF;
+                            v1 = INF;
+                            rb = 0.f;
                         }
                     }
-                    V left = recv;
-                    if constexpr (Md::kRebase) left = recv + (rb - B);  // into this thread's base
-                    const V conv = left;
-                    const V xv = xs[r];
+                    if (act) {
+                        if (p == 0) {
+                            // new sweep: load the strip's reference samples; the
+                            // previous row is the virtual all-zero row -1
+                            base = s * S + threadIdx.x * W;
 #pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        const V up = D[k];
-                        const V nv = Md::cell(xv, y[k], up, diag, left);
-                        diag = up;
-                        left = nv;
-                        D[k] = nv;
-                    }
-                    diag = conv;
-                    if (r == n - 1) {
-#pragma unroll
-                        for (int k = 0; k < W; ++k) {
-                            V v = D[k];
-                            if constexpr (Md::kRebase) v = B + D[k];
-                            if (base + k < M && v < best) {
-                                best = v;
-                                best_col = base + k;
+                            for (int k = 0; k < W; ++k) {
+                                const int col = base + k;
+                                y[k] = col < M ? Md::widen(ref[col]) : Md::zero();
+                                prev[k] = Md::zero();
+                            }
+                            diag = Md::zero();
+                            B = 0.f;
+                            ck = nullptr;
+                            if (a.ckpt) {
+                                const int edge = base + W;
+                                if (edge % a.K == 0 && edge / a.K <= a.nblk)
+                                    ck = a.ckpt + (start - first_start) * a.nblk +
+                                         static_cast<int64_t>(edge / a.K - 1) * n;
                             }
                         }
-                    }
-                    if (lane == 31) {
-                        if (warp < P - 1) {
-                            ringv_out[t & (kRing - 1)] = D[W - 1];
-                            if constexpr (Md::kRebase) ringb_out[t & (kRing - 1)] = B;
-                        } else {
-                            colv[r] = D[W - 1];
-                            if constexpr (Md::kRebase) colb[r] = B;
+                        V left0 = v0, left1 = v1;
+                        if constexpr (Md::kRebase) {
+                            const float dd = rb - B;  // into this thread's base
+                            left0 = v0 + dd;
+                            left1 = v1 + dd;
+                        }
+                        const V2 xp = xs2[p];
+                        tile_step<Md, W>(prev, A, y, xp.x, xp.y, diag, left0, left1);
+                        diag = left1;
+                        if (p == lastp) {
+                            // row n-1 is the pair's first row (odd n) or its second
+#pragma unroll
+                            for (int k = 0; k < W; ++k) {
+                                V v = (n & 1) ? A[k] : prev[k];
+                                if constexpr (Md::kRebase) v = v + B;
+                                if (base + k < M && v < best) {
+                                    best = v;
+                                    best_col = base + k;
+                                }
+                            }
+                        }
+                        if (lane == 31) {
+                            E e;
+                            e.v0 = A[W - 1];
+                            e.v1 = prev[W - 1];
+                            e.b = B;
+                            e.pad = 0;
+                            if (warp < P - 1)
+                                ring_out[t & (kRing - 1)] = e;
+                            else
+                                colbuf[p] = e;
+                        }
+                        if (ck) {
+                            ck[2 * p] = static_cast<float>(A[W - 1]) + B;
+                            if (2 * p + 1 < n) ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
                         }
                     }
-                    if (ck) ck[r] = static_cast<float>(D[W - 1]) + B;
-                }
-                if (++r == Np) {
-                    r = 0;
-                    ++s;
+                    if (++p == Pp) {
+                        p = 0;
+                        ++s;
+                    }
                 }
             }
             __syncthreads();
@@ -313,7 +444,9 @@ cudaError_t launch_t(const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
 {
     switch (plan.W) {
     case 8: return launch_w<Tin, 8>(plan, a, s);
+    case 12: return launch_w<Tin, 12>(plan, a, s);
     case 16: return launch_w<Tin, 16>(plan, a, s);
+    case 24: return launch_w<Tin, 24>(plan, a, s);
     case 32: return launch_w<Tin, 32>(plan, a, s);
     default: return cudaErrorInvalidValue;
     }
@@ -334,7 +467,9 @@ int occupancy_t(int W, int block, int smem)
 {
     switch (W) {
     case 8: return occupancy_w<Tin, 8>(block, smem);
+    case 12: return occupancy_w<Tin, 12>(block, smem);
     case 16: return occupancy_w<Tin, 16>(block, smem);
+    case 24: return occupancy_w<Tin, 24>(block, smem);
     case 32: return occupancy_w<Tin, 32>(block, smem);
     default: return 0;
     }
@@ -342,13 +477,14 @@ int occupancy_t(int W, int block, int smem)
 
 }  // namespace
 
-bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 32; }
+bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 12 || W == 16 || W == 24 || W == 32; }
 
 int fwd_smem_bytes(sdtw_dtype, int N, int P)
 {
-    // xs[N] + column values and bases [2N] + ring values and bases [2P*kRing]
-    // + reduction (value, index)[P]; 4-byte elements
-    return 4 * (3 * N + 2 * P * kRing + 2 * P);
+    // ring [P][kRing] and column buffer [Npad/2] of 16-byte edges, query samples
+    // [Npad] and the reduction (value, index)[P], 4-byte elements
+    const int npad = (N + 1) & ~1;
+    return 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P)
@@ -356,8 +492,9 @@ int64_t fwd_total_steps(int64_t M, int N, int W, int P)
     const int64_t S = static_cast<int64_t>(32) * P * W;
     const int64_t nsw = (M + S - 1) / S;
     const int64_t lag_last = static_cast<int64_t>(P - 1) * (32 + kChunk) + 31;
-    const int64_t Np = std::max<int64_t>(N, lag_last + kChunk);
-    return (nsw - 1) * Np + N + lag_last;
+    const int64_t npairs = (N + 1) / 2;
+    const int64_t Pp = std::max<int64_t>(npairs, lag_last + kChunk);
+    return (nsw - 1) * Pp + npairs + lag_last;
 }
 
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem)

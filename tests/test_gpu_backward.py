@@ -70,31 +70,61 @@ def check_validity(w, cost, end, gq, gr, path, g, idx, oracle_costs):
     return gy_sum
 
 
+TIE = 1e-5    # a walk-back step is a near-tie when its two best neighbours differ by < TIE * cost
+
+
+def compare_with_oracle_paths(w, end, gq, path, g, idx, oracle_costs, oracle_ends):
+    """Follow the GPU path and the oracle's walk-back from the end cell: they must
+    agree until their first divergence, and a divergence may only start at a step
+    where the oracle's best two neighbours are within FP32 resolution (a near-tie).
+    Where the whole path agrees, the gradients must match the oracle's.
+    Returns (queries with identical paths, matched cells, total cells)."""
+    y = w.ref.astype(np.float64)
+    same = matched = total = 0
+    for k, q in enumerate(idx):
+        if int(end[q]) != int(oracle_ends[k]):
+            continue                      # a tied end: covered by the end-index rule
+        x = w.query(q).astype(np.float64)
+        cells, margins = oracle.walkback(x, y, int(oracle_ends[k]))
+        lo, hi = _rows(w, path, q)
+        gcells = oracle.cells_from_intervals(lo, hi)
+        L = min(len(cells), len(gcells))
+        diff = np.nonzero((cells[:L] != gcells[:L]).any(axis=1))[0]
+        total += len(cells)
+        if len(diff) == 0 and len(cells) == len(gcells):
+            same += 1
+            matched += len(cells)
+            gx, _ = oracle.path_gradient(x, y, cells, g=float(g[q]))
+            assert np.all(np.abs(_gq(w, gq, q) - gx) <= GTOL * np.abs(gx).max() + 1e-6), q
+            continue
+        first = int(diff[0]) if len(diff) else L
+        matched += first
+        assert first >= 1, q              # the end cell itself is shared
+        tol = TIE * oracle_costs[k] + 1e-6 * len(x)
+        assert 0 <= margins[first - 1] <= tol, (q, first, margins[first - 1], tol)
+    return same, matched, total
+
+
 def test_grad_subset_matches_oracle_paths(gpu):
-    """8 x 64 vs 512: exact path agreement away from near-ties, and gradients."""
+    """8 x 64 vs 512: the walk-back follows the oracle's up to FP32 near-ties."""
     w = inputs.grad_subset()
     g = np.linspace(0.5, 2.0, w.B)
     cost, end, gq, gr, path, gd = run_bwd(gpu, w, grad_cost=g)
-    y = w.ref.astype(np.float64)
     oc, oe = oracle.forward_batch(w.ref, w.queries)
     gy_sum = check_validity(w, cost, end, gq, gr, path, gd, range(w.B), oc)
     assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
-    exact = 0
-    for q in range(w.B):
-        x = w.query(q).astype(np.float64)
-        cells, margins = oracle.walkback(x, y, int(oe[q]))
-        # a step whose best and second-best neighbours differ by less than 20x the
-        # FP32 error of D (about 1e-6 relative with per-lane rebasing) may go either way
-        near_tie = (margins[margins >= 0] <= 2e-5 * oc[q] + 1e-6 * len(x)).any()
-        if near_tie or int(end[q]) != int(oe[q]):
-            continue
-        lo, hi = oracle.intervals_from_cells(cells, len(x))
-        glo, ghi = _rows(w, path, q)
-        assert np.array_equal(glo, lo) and np.array_equal(ghi, hi), q
-        gx, _ = oracle.path_gradient(x, y, cells, g=float(gd[q]))
-        assert np.all(np.abs(gq[q] - gx) <= GTOL * np.abs(gx).max() + 1e-6)
-        exact += 1
-    assert exact >= 4
+    same, matched, total = compare_with_oracle_paths(w, end, gq, path, gd, range(w.B), oc, oe)
+    assert same >= 2 and matched >= 0.5 * total
+
+
+def test_walkback_tie_rule_on_many_queries(gpu):
+    """48 queries x 64..200 samples: every divergence from the oracle's path starts at a near-tie."""
+    w = inputs.tiny(B=48, N=150, M=3000, seed=97)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w)
+    oc, oe = oracle.forward_batch(w.ref, w.queries)
+    check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+    same, matched, total = compare_with_oracle_paths(w, end, gq, path, g, range(w.B), oc, oe)
+    assert same >= 5 and matched >= 0.5 * total
 
 
 @pytest.mark.parametrize("B,N,M,K", [(4, 50, 700, 64), (3, 300, 2000, 128), (2, 129, 5000, 256),

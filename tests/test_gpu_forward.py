@@ -52,7 +52,7 @@ def test_shapes_fp32(gpu, B, N, M):
     assert parity.check_forward_f32(w.ref, w.query, range(B), cost, end) == []
 
 
-@pytest.mark.parametrize("W", [8, 16, 32])
+@pytest.mark.parametrize("W", [8, 12, 16, 24, 32])
 @pytest.mark.parametrize("P", [1, 2, 4, 8, 16])
 def test_every_plan_fp32(gpu, W, P):
     w = inputs.tiny(B=3, N=90, M=6000, seed=77)
@@ -60,7 +60,7 @@ def test_every_plan_fp32(gpu, W, P):
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
 
-@pytest.mark.parametrize("W", [8, 16, 32])
+@pytest.mark.parametrize("W", [8, 12, 16, 24, 32])
 @pytest.mark.parametrize("P", [1, 4, 16])
 def test_every_plan_i8_bit_exact(gpu, W, P):
     w = inputs.paper_i8(B=4, N=70, M=5000, seed=78)

@@ -1,16 +1,21 @@
 """CPU model of the forward kernel's schedule (paper Section 5.2 wavefront).
 
 The CUDA forward (csrc/sdtw_forward.cu) runs a chain of 32*P threads, each
-owning W reference columns; thread l lags thread l-1 by one step inside a
-warp, warp w lags warp w-1 by 32 + kChunk steps, values cross warps through a
-ring of kRing shared-memory slots and cross sweeps through a column buffer,
-with one CTA barrier after every kChunk steps.  This test replays exactly
-that index arithmetic step by step (numpy over threads) and checks, for many
-shapes including ragged tails, tiny queries and short references:
+owning W reference columns and advancing two query rows per step (a 2 x W
+tile); thread l lags thread l-1 by one step inside a warp, warp w lags warp
+w-1 by 32 + kChunk steps, tile edges cross warps through a ring of kRing
+shared-memory slots and cross sweeps through a column buffer indexed by row
+pair, with one CTA barrier after every kChunk steps.  Chunks in which no
+thread of a warp starts a sweep, idles or meets the bottom row take a fast
+path.  This test replays exactly that index arithmetic step by step (numpy
+over threads) and checks, for many shapes including ragged tails, odd and tiny
+queries and short references:
 
-* every shared-memory read sees the value written for the same query row by
-  the producer thread, written in an earlier barrier interval (no race);
+* every shared-memory read sees the edge written for the same row pair by the
+  producer thread, written in an earlier barrier interval (no race);
 * no slot is overwritten before its reader's barrier interval has passed;
+* the fast-path test admits only chunks in which every thread of the warp is
+  active, past its sweep's first pair and before its last pair;
 * the bottom row it produces equals the oracle's last DP row exactly
   (float64 arithmetic), and the (cost, end) reduction matches;
 * checkpoint columns land at the documented offsets with the DP's values.
@@ -34,101 +39,133 @@ def simulate_forward(x, y, P, W, K=None):
     warp, lane = lane_ids // 32, lane_ids % 32
     lag = warp * (32 + K_CHUNK) + lane
     lag_last = (P - 1) * (32 + K_CHUNK) + 31
-    Np = max(n, lag_last + K_CHUNK)
-    total = (nsw - 1) * Np + n + lag_last
+    npairs = (n + 1) // 2
+    lastp = npairs - 1
+    Pp = max(npairs, lag_last + K_CHUNK)
+    total = (nsw - 1) * Pp + npairs + lag_last
+    xs = np.concatenate([x, [0.0] * (2 * npairs - n)])
     chunk = lambda t: t // K_CHUNK  # noqa: E731  (barrier after every K_CHUNK steps)
 
     INF = np.inf
-    D = np.zeros((L, W))
+    prev = np.zeros((L, W))        # latest row of each strip
+    a_last = np.zeros(L)           # right-hand cell of the pair's first row
     yv = np.zeros((L, W))
     diag = np.zeros(L)
-    r = -lag.copy()
+    p = -lag.copy()
     s = np.zeros(L, dtype=np.int64)
     base = lane_ids * W
-    ring_val = np.zeros((P, K_RING))
-    ring_wstep = np.full((P, K_RING), -10**9)
-    ring_rstep = np.full((P, K_RING), -10**9)
-    col_val = np.zeros(n)
-    col_wstep = np.full(n, -10**9)
-    col_rstep = np.full(n, -10**9)
+    ring = np.zeros((P, K_RING, 2))
+    ring_w = np.full((P, K_RING), -10**9)
+    ring_r = np.full((P, K_RING), -10**9)
+    col = np.zeros((npairs, 2))
+    col_w = np.full(npairs, -10**9)
+    col_r = np.full(npairs, -10**9)
     last_row = np.full(M, np.nan)
     ckpt = {}
+    fast_chunks = 0
     for t in range(total):
-        last = D[:, W - 1].copy()
-        recv = np.roll(last, 1)
-        act = (r >= 0) & (r < n) & (s < nsw)
+        if t % K_CHUNK == 0:
+            for w in range(P):
+                gmin = t - w * (32 + K_CHUNK) - 31
+                gmax = t - w * (32 + K_CHUNK) + K_CHUNK - 1
+                fast = gmin >= 0
+                if fast:
+                    sw = gmin // Pp
+                    fast = gmax // Pp == sw and sw < nsw and gmin - sw * Pp >= 1 and gmax - sw * Pp <= lastp - 1
+                if fast:
+                    fast_chunks += 1
+                    for u in range(K_CHUNK):
+                        for l in range(32 * w, 32 * w + 32):
+                            pp = p[l] + u
+                            assert 1 <= pp <= lastp - 1 and s[l] < nsw, "fast path admitted a special step"
+        send = np.stack([a_last, prev[:, W - 1]], axis=1)
+        recv = np.roll(send, 1, axis=0)
+        act = (p >= 0) & (p < npairs) & (s < nsw)
         for l in np.nonzero(lane == 0)[0]:
             w = warp[l]
             if w > 0:
                 slot = (t - K_CHUNK - 1) & (K_RING - 1)
                 if act[l]:
-                    assert ring_wstep[w, slot] == t - K_CHUNK - 1, "ring read of a different row"
-                    assert chunk(ring_wstep[w, slot]) < chunk(t), "ring read without a barrier"
-                    ring_rstep[w, slot] = t
-                recv[l] = ring_val[w, slot]
+                    assert ring_w[w, slot] == t - K_CHUNK - 1, "ring read of a different pair"
+                    assert chunk(ring_w[w, slot]) < chunk(t), "ring read without a barrier"
+                    ring_r[w, slot] = t
+                recv[l] = ring[w, slot]
+            elif act[l] and s[l] > 0:
+                pp = p[l]
+                assert col_w[pp] == (s[l] - 1) * Pp + pp + lag_last, "column read of a different sweep"
+                assert chunk(col_w[pp]) < chunk(t), "column read without a barrier"
+                col_r[pp] = t
+                recv[l] = col[pp]
             else:
-                if act[l] and s[l] > 0:
-                    rr = r[l]
-                    assert col_wstep[rr] == (s[l] - 1) * Np + rr + lag_last, "column read of a different sweep"
-                    assert chunk(col_wstep[rr]) < chunk(t), "column read without a barrier"
-                    col_rstep[rr] = t
-                    recv[l] = col_val[rr]
-                else:
-                    recv[l] = INF
+                recv[l] = INF
         for l in np.nonzero(act)[0]:
-            if r[l] == 0:
+            if p[l] == 0:
                 base[l] = s[l] * S + l * W
                 cols = base[l] + np.arange(W)
                 yv[l] = np.where(cols < M, y[np.minimum(cols, M - 1)], 0.0)
-                D[l] = 0.0
+                prev[l] = 0.0
                 diag[l] = 0.0
-            xv = x[r[l]]
-            left = recv[l]
-            for k in range(W):
-                up = D[l, k]
-                d = xv - yv[l, k]
-                nv = d * d + min(up, diag[l], left)
-                diag[l] = up
-                left = nv
-                D[l, k] = nv
-            diag[l] = recv[l]
-            if r[l] == n - 1:
+            x0, x1 = xs[2 * p[l]], xs[2 * p[l] + 1]
+            left0, left1 = recv[l]
+            A = np.zeros(W)
+            for k in range(W + 1):          # the tile's anti-diagonals, in kernel order
+                if k < W:
+                    up = prev[l, k]
+                    dg = diag[l] if k == 0 else prev[l, k - 1]
+                    lf = left0 if k == 0 else A[k - 1]
+                    d = x0 - yv[l, k]
+                    A[k] = d * d + min(up, dg, lf)
+                if k >= 1:
+                    j = k - 1
+                    up = A[j]
+                    dg = left0 if j == 0 else A[j - 1]
+                    lf = left1 if j == 0 else prev[l, j - 1]
+                    d = x1 - yv[l, j]
+                    prev[l, j] = d * d + min(up, dg, lf)
+            a_last[l] = A[W - 1]
+            diag[l] = left1
+            if p[l] == lastp:
+                row = A if n % 2 else prev[l]
                 for k in range(W):
                     if base[l] + k < M:
-                        last_row[base[l] + k] = D[l, k]
+                        last_row[base[l] + k] = row[k]
             if lane[l] == 31:
+                edge = (A[W - 1], prev[l, W - 1])
                 if warp[l] < P - 1:
                     w2, slot = warp[l] + 1, t & (K_RING - 1)
-                    assert chunk(ring_rstep[w2, slot]) < chunk(t) or ring_rstep[w2, slot] < 0, "ring overwrite race"
-                    assert ring_wstep[w2, slot] < 0 or ring_rstep[w2, slot] > ring_wstep[w2, slot] or \
-                        ring_wstep[w2, slot] < 0, "ring value overwritten before it was read"
-                    ring_val[w2, slot] = D[l, W - 1]
-                    ring_wstep[w2, slot] = t
+                    if ring_r[w2, slot] > ring_w[w2, slot]:     # the value there was consumed:
+                        assert chunk(ring_r[w2, slot]) < chunk(t), "ring overwrite race"
+                    ring[w2, slot] = edge
+                    ring_w[w2, slot] = t
                 else:
-                    rr = r[l]
-                    if col_wstep[rr] >= 0 and s[l] > 0:
-                        assert col_rstep[rr] > col_wstep[rr], "column value overwritten before it was read"
-                        assert chunk(col_rstep[rr]) < chunk(t), "column overwrite race"
-                    col_val[rr] = D[l, W - 1]
-                    col_wstep[rr] = t
+                    pp = p[l]
+                    if col_w[pp] >= 0 and s[l] > 0:
+                        assert col_r[pp] > col_w[pp], "column value overwritten before it was read"
+                        assert chunk(col_r[pp]) < chunk(t), "column overwrite race"
+                    col[pp] = edge
+                    col_w[pp] = t
             if K:
-                edge = base[l] + W
-                if edge % K == 0 and edge // K <= M // K:
-                    ckpt[(edge // K - 1, r[l])] = D[l, W - 1]
-        r += 1
-        wrap = r == Np
-        r[wrap] = 0
+                e = base[l] + W
+                if e % K == 0 and e // K <= M // K:
+                    ckpt[(e // K - 1, 2 * p[l])] = A[W - 1]
+                    if 2 * p[l] + 1 < n:
+                        ckpt[(e // K - 1, 2 * p[l] + 1)] = prev[l, W - 1]
+        p += 1
+        wrap = p == Pp
+        p[wrap] = 0
         s[wrap] += 1
-    return last_row, ckpt
+    return last_row, ckpt, fast_chunks
 
 
 CASES = [
     # (P, W, n, M)
     (1, 4, 40, 300),     # one warp, several sweeps, ragged tail
-    (2, 4, 40, 600),     # inter-warp ring, query shorter than the chain lag (padded period)
-    (2, 2, 130, 700),    # query longer than the chain lag
+    (2, 4, 41, 600),     # inter-warp ring, odd query shorter than the chain lag (padded period)
+    (2, 2, 260, 700),    # query longer than the chain lag: fast-path chunks
+    (1, 2, 301, 900),    # odd query, one warp, fast-path chunks
     (3, 2, 5, 1000),     # three warps, tiny query
     (2, 4, 1, 333),      # one-row query
+    (2, 4, 2, 333),      # one pair
     (2, 8, 70, 20),      # reference shorter than one sweep
     (1, 2, 33, 1),       # one-column reference
 ]
@@ -139,8 +176,10 @@ def test_schedule_reproduces_last_row(oracle_mod, P, W, n, M):
     rng = np.random.default_rng(100 * P + 10 * W + n)
     x = rng.standard_normal(n)
     y = rng.standard_normal(M)
-    last_row, _ = simulate_forward(x, y, P, W)
+    last_row, _, fast = simulate_forward(x, y, P, W)
     c, e, row = oracle_mod.forward(x, y, last_row=True)
+    if n > 200:
+        assert fast > 0
     assert not np.isnan(last_row).any()
     assert np.array_equal(last_row, row)
     assert np.min(last_row) == c and int(np.argmin(last_row)) == e
@@ -152,7 +191,7 @@ def test_schedule_checkpoints(oracle_mod):
     x = w.query(0).astype(np.float64)
     y = w.ref.astype(np.float64)
     K = 16
-    _, ck = simulate_forward(x, y, 2, 4, K=K)
+    _, ck, _ = simulate_forward(x, y, 2, 4, K=K)
     assert len(ck) == (len(y) // K) * len(x)
     for b in (0, 3, len(y) // K - 1):
         col = (b + 1) * K - 1
