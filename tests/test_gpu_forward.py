@@ -69,6 +69,19 @@ def test_every_plan_i8_bit_exact(gpu, W, P):
     assert parity.check_forward_i8(w.ref, w.query, range(w.B), cost, end) == []
 
 
+@pytest.mark.parametrize("W", [8, 16, 24])
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_fast_path_plans(gpu, W, P):
+    # queries long enough that most chunks take the fast path; odd and even lengths
+    for N in (1501, 1200):
+        w = inputs.tiny(B=2, N=N, M=20000, seed=79 + N)
+        cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P)
+        assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
+        wi = inputs.paper_i8(B=2, N=N, M=20000, seed=80 + N)
+        cost, end = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P)
+        assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
+
+
 def test_exact_cut_has_zero_cost(gpu):
     w = inputs.tiny(B=1, N=10, M=3000, seed=5)
     y = w.ref
