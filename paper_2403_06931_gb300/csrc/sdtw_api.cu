@@ -74,8 +74,10 @@ struct sdtw_ctx {
     int32_t* d_order = nullptr;
 
     // backward workspace
-    float* d_ckpt = nullptr;
+    float* d_ckpt = nullptr;   // column checkpoints
     size_t ckpt_elems = 0;
+    float* d_rowck = nullptr;  // row checkpoints
+    size_t rowck_elems = 0;
     int K_min = 0;        // smallest checkpoint stride the workspace holds for a full chunk
     int K = 0;            // checkpoint stride in use
     int bwd_chunk = 0;    // queries per backward chunk
@@ -199,6 +201,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     a.cost = cost;
     a.end = end;
     a.ckpt = ckpt;
+    a.rowck = ckpt ? c->d_rowck : nullptr;
     a.K = ckpt ? c->K : 1;
     a.nblk = ckpt ? nblk_of(M, c->K) : 0;
     a.ckpt_rows = ckpt ? static_cast<int64_t>(c->bwd_chunk) * c->cfg.max_query_len : 0;
@@ -235,8 +238,8 @@ sdtw_status alloc_backward(sdtw_ctx* c)
     const size_t fixed = c->ws_bytes + 12 * static_cast<size_t>(f.max_batch);
     for (int i = 0; i < nK; ++i) {
         const int K = Ks[i];
-        // per query: checkpoints N*floor(M/K) floats, gradient row M floats, span, cost/end scratch
-        const size_t per_q = 4 * static_cast<size_t>(N) * nblk_of(M, K) + 4 * static_cast<size_t>(M) + 32;
+        // per query: column and row checkpoints, gradient row M floats, span
+        const size_t per_q = 4 * sdtw::ckpt_floats_per_query(N, M, K) + 4 * static_cast<size_t>(M) + 32;
         if (fixed + per_q > c->cap) continue;
         const int64_t fit = static_cast<int64_t>((c->cap - fixed) / per_q);
         const int chunk = static_cast<int>(std::min<int64_t>(fit, f.max_batch));
@@ -244,8 +247,12 @@ sdtw_status alloc_backward(sdtw_ctx* c)
         c->K = f.ckpt_stride > 0 ? f.ckpt_stride : 256;
         c->bwd_chunk = chunk;
         c->ckpt_elems = static_cast<size_t>(N) * nblk_of(M, K) * chunk;
+        c->rowck_elems = static_cast<size_t>(static_cast<int64_t>(chunk) * N / K) * static_cast<size_t>(M);
         sdtw_status s;
         if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_ckpt), 4 * std::max<size_t>(c->ckpt_elems, 1))) != SDTW_OK)
+            return s;
+        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_rowck), 4 * std::max<size_t>(c->rowck_elems, 1))) !=
+            SDTW_OK)
             return s;
         if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_gyq), 4 * static_cast<size_t>(M) * chunk)) != SDTW_OK)
             return s;
@@ -265,6 +272,7 @@ void free_all(sdtw_ctx* c)
     dev_free(c, c->d_queue, sizeof(int));
     dev_free(c, c->d_order, 4 * static_cast<size_t>(c->cfg.max_batch));
     dev_free(c, c->d_ckpt, 4 * std::max<size_t>(c->ckpt_elems, 1));
+    dev_free(c, c->d_rowck, 4 * std::max<size_t>(c->rowck_elems, 1));
     dev_free(c, c->d_gyq, 4 * static_cast<size_t>(c->cfg.max_ref_len) * c->bwd_chunk);
     dev_free(c, c->d_span, 16 * static_cast<size_t>(c->bwd_chunk));
     dev_free(c, c->d_cost_tmp, 4 * static_cast<size_t>(c->cfg.max_batch));
@@ -433,6 +441,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         a.grad_queries = grad_queries;
         a.path = path;
         a.ckpt = ctx->d_ckpt;
+        a.rowck = ctx->d_rowck;
         a.K = ctx->K;
         a.nblk = nblk_of(M, ctx->K);
         a.ckpt_rows = static_cast<int64_t>(ctx->bwd_chunk) * ctx->cfg.max_query_len;

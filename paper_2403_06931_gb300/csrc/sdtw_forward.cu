@@ -45,8 +45,10 @@
 // sender's base and are converted on receipt; a sweep starts from base 0.  The
 // drift falls below 1e-7 and the worst error to ~1.5e-6.
 //
-// Optional checkpoints for the backward pass: a thread whose strip ends at a
-// multiple of K stores that column's absolute D value for every row.
+// Optional checkpoints for the backward pass, taken as the wavefront passes:
+// a thread whose strip ends at a multiple of K stores that column's absolute D
+// value for every row, and every thread stores its strip of every K-th row
+// (coalesced across the chain).  The backward recomputes K x K tiles from them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -208,6 +210,7 @@ fwd_chain_kernel(const FwdArgs a)
         }
         V diag = Md::zero();
         float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
+        float* rck = a.rowck ? a.rowck + ((start - first_start) / a.K) * a.M : nullptr;
         V best = INF;
         int best_col = INT_MAX;
         int p = -lag;   // row pair of this thread's tile in sweep s (negative: not started)
@@ -285,6 +288,12 @@ fwd_chain_kernel(const FwdArgs a)
                     if (ck) {
                         ck[2 * p] = static_cast<float>(A[W - 1]) + B;
                         ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
+                    }
+                    if (rck && ((2 * p + 2) & (a.K - 1)) == 0) {
+                        float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.K - 1) * a.M + base;
+#pragma unroll
+                        for (int k = 0; k < W; ++k)
+                            if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;
                     }
                     ++p;
                 }
@@ -370,6 +379,12 @@ fwd_chain_kernel(const FwdArgs a)
                         if (ck) {
                             ck[2 * p] = static_cast<float>(A[W - 1]) + B;
                             if (2 * p + 1 < n) ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
+                        }
+                        if (rck && ((2 * p + 2) & (a.K - 1)) == 0 && 2 * p + 1 < n) {
+                            float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.K - 1) * a.M + base;
+#pragma unroll
+                            for (int k = 0; k < W; ++k)
+                                if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;
                         }
                     }
                     if (++p == Pp) {

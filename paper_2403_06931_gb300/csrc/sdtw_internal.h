@@ -37,8 +37,14 @@ struct FwdArgs {
     int32_t B_total;  // queries in the whole batch (offsets has B_total + 1 entries)
     void* cost;
     int64_t* end;
-    float* ckpt;  // nullptr: no checkpoints; else query q at (start_q - start_q0) * nblk, n_q floats per block
-    int32_t K;    // checkpoint stride (columns); multiple of the segment width
+    // Checkpoints for the backward pass (nullptr: none), absolute D values:
+    //   ckpt   every K-th column: query q at (start_q - start_q0) * nblk, block b
+    //          (column (b+1)K-1) at b * n_q, one value per row;
+    //   rowck  every K-th row: query q at floor((start_q - start_q0) / K) * M,
+    //          stored row m (row (m+1)K-1) at m * M, one value per column.
+    float* ckpt;
+    float* rowck;
+    int32_t K;    // checkpoint stride (rows and columns); multiple of the segment width
     int64_t nblk; // floor(M / K)
     int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
     int* status;
@@ -76,8 +82,9 @@ struct BwdArgs {
     const float* grad_cost;
     float* grad_queries;
     int32_t* path;
-    const float* ckpt;  // checkpoints of queries q0 .. q0+B-1: query q at (start_q - start_q0) * nblk
-    int32_t K;
+    const float* ckpt;   // column checkpoints of queries q0 .. q0+B-1 (layout as FwdArgs)
+    const float* rowck;  // row checkpoints (layout as FwdArgs)
+    int32_t K;           // tile side: checkpoint stride in rows and columns
     int64_t nblk;
     int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
@@ -88,6 +95,7 @@ struct BwdArgs {
 // Backward launches (sdtw_backward.cu).
 bool bwd_stride_supported(int K);
 int bwd_smem_bytes(int N, int K);
+size_t ckpt_floats_per_query(int64_t N, int64_t M, int K);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);

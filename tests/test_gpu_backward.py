@@ -158,7 +158,9 @@ def test_chunked_and_recomputed_backward_are_identical(gpu):
     w = inputs.tiny(B=9, N=200, M=4000, seed=81)
     a = run_bwd(gpu, w, keep=True)                          # checkpoints from the forward
     b = run_bwd(gpu, w, keep=False)                         # backward re-runs the forward
-    per_q = 4 * 200 * (4000 // 64) + 4 * 4000 + 32
+    # per query at the smallest stride (64): a column every 64 columns, a row
+    # every 64 rows, one gradient row, span
+    per_q = 4 * (200 * (4000 // 64) + (200 // 64) * 4000) + 4 * 4000 + 32
     c = run_bwd(gpu, w, keep=False, mem_cap_bytes=3 * per_q + 200_000)   # forces chunks of queries
     for u, v in ((a, b), (a, c)):
         for k in range(5):

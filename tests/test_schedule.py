@@ -150,6 +150,10 @@ def simulate_forward(x, y, P, W, K=None):
                     ckpt[(e // K - 1, 2 * p[l])] = A[W - 1]
                     if 2 * p[l] + 1 < n:
                         ckpt[(e // K - 1, 2 * p[l] + 1)] = prev[l, W - 1]
+                if (2 * p[l] + 2) % K == 0 and 2 * p[l] + 1 < n:
+                    for k in range(W):
+                        if base[l] + k < M:
+                            ckpt[("row", (2 * p[l] + 2) // K - 1, base[l] + k)] = prev[l, k]
         p += 1
         wrap = p == Pp
         p[wrap] = 0
@@ -192,7 +196,13 @@ def test_schedule_checkpoints(oracle_mod):
     y = w.ref.astype(np.float64)
     K = 16
     _, ck, _ = simulate_forward(x, y, 2, 4, K=K)
-    assert len(ck) == (len(y) // K) * len(x)
+    rows = {k: v for k, v in ck.items() if k[0] == "row"}
+    assert len(ck) - len(rows) == (len(y) // K) * len(x)
+    assert len(rows) == (len(x) // K) * len(y)
+    for m in range(len(x) // K):
+        i = (m + 1) * K - 1
+        _, _, row = oracle_mod.forward(x[:i + 1], y, last_row=True)
+        assert all(rows[("row", m, j)] == row[j] for j in range(len(y)))
     for b in (0, 3, len(y) // K - 1):
         col = (b + 1) * K - 1
         for i in (0, 7, len(x) - 1):
