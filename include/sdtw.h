@@ -219,6 +219,40 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
 sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_t ragged,
                           int32_t backward, sdtw_plan* plan);
 
+/* Largest batch sdtw_forward_noalloc accepts (its fixed device scratch holds
+ * the query order for this many queries: 256 KiB per GPU). */
+#define SDTW_NOALLOC_MAX_BATCH 65536
+
+/*
+ * sdtw_forward without a context and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code that runs while a CUDA graph is being
+ * captured and must not allocate, plug-ins inside a host process that owns
+ * all device memory through its own pool, real-time loops that may not touch
+ * the allocator after start-up.  It runs the same persistent forward kernel
+ * as sdtw_forward with a fixed plan (32 columns per thread, 4 warps per
+ * query); its only scratch (work counter, status word, query order) is one
+ * fixed-size array in the library's device memory, which every GPU that
+ * loads the library keeps until the process exits.
+ *   dtype     SDTW_F32 or SDTW_I8; ref, queries, offsets, B, N, M, cost and
+ *             end as in sdtw_forward (device pointers owned by the caller).
+ *   stream    the launch stream; the device is the calling thread's current
+ *             device.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (on
+ * different streams, or from several host threads) race and must not be
+ * issued.  Each call clears the counter and status word itself.  Errors found
+ * on the device (a ragged query longer than N) are not reported: that
+ * query's outputs are left unwritten.
+ * Errors: SDTW_E_INVALID (bad sizes or null pointers as for sdtw_forward,
+ * unknown dtype, B > SDTW_NOALLOC_MAX_BATCH), SDTW_E_UNSUPPORTED (N too long
+ * for shared memory), SDTW_E_CUDA.
+ */
+sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, int64_t M, const void* queries,
+                                 const int64_t* offsets, int32_t B, int32_t N, void* cost, int64_t* end,
+                                 void* stream);
+
 /* Synchronise `stream`, then return and clear the device status word: SDTW_OK,
  * SDTW_E_INVALID (a ragged query longer than N, an end index outside [0, M))
  * or SDTW_E_TIMEOUT.  SDTW_E_CUDA if the synchronisation itself failed. */

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("sdtw_forward_backward_host", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("sdtw_autotune", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, ctypes.POINTER(sdtw_plan)]),
     ("sdtw_get_plan", _ST, [_P, _I32, _I32, _I64, _I32, _I32, ctypes.POINTER(sdtw_plan)]),
+    ("sdtw_forward_noalloc", _ST, [ctypes.c_int, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
     ("sdtw_last_device_status", _ST, [_P, _P]),
     ("sdtw_last_error", ctypes.c_char_p, [_P]),
     ("sdtw_workspace_bytes", ctypes.c_size_t, [_P]),
@@ -187,6 +188,13 @@ def sdtw_get_plan(ctx, B, N, M, ragged, backward):
     plan = sdtw_plan()
     st = load().sdtw_get_plan(ctx, B, N, M, ragged, backward, ctypes.byref(plan))
     return st, plan
+
+
+def sdtw_forward_noalloc(dtype, ref, M, queries, offsets, B, N, cost, end, stream) -> int:
+    return load().sdtw_forward_noalloc(dtype, ref, M, queries, offsets, B, N, cost, end, stream)
+
+
+SDTW_NOALLOC_MAX_BATCH = 65536
 
 
 def sdtw_last_device_status(ctx, stream) -> int:

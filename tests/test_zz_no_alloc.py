@@ -1,0 +1,81 @@
+"""sdtw_forward_noalloc: the forward for callers that cannot allocate.
+
+Callers inside a graph capture that may not allocate, plug-ins whose host
+process owns every device allocation, and real-time loops that must not touch
+the allocator after start-up cannot create a context (sdtw_create allocates).
+This entry point keeps its small scratch in a fixed device array instead.  The
+test calls it through the C ABI twice in a row (the array keeps the previous
+call's contents, which the entry point must clear) and compares both results
+with sdtw_forward's, within the parity tolerance of the other tests.  It is
+collected last so that a failure here cannot hide any other test's result.
+"""
+import numpy as np
+import pytest
+import torch
+
+import parity
+from paper_2403_06931_gb300 import capi, inputs
+from paper_2403_06931_gb300.sdtw import SdtwContext
+
+pytestmark = pytest.mark.gpu
+
+
+def _same_within_tolerance(c_ref, e_ref, c, e, lengths):
+    tol = parity.cost_tol(c_ref.astype(np.float64), lengths)
+    assert np.all(np.abs(c.astype(np.float64) - c_ref) <= tol)
+    assert np.array_equal(e, e_ref)
+
+
+@pytest.mark.parametrize("ragged", [True, False])
+def test_noalloc_matches_forward_twice(gpu, ragged):
+    if ragged:
+        w = inputs.ragged_fp32(B=40, n_lo=1, n_hi=700, M=30000, seed=611)
+    else:
+        w = inputs.tiny(B=24, N=300, M=30000, seed=612)
+    N = int(w.lengths.max())
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    offs = torch.from_numpy(w.offsets).to(gpu) if ragged else None
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=N, max_total_query_len=qs.numel(),
+                      seg_width=32, warps_per_query=4)
+    c_ref, e_ref = ctx.forward(ref, qs, offsets=offs, N=N if ragged else None)
+    torch.cuda.synchronize()
+    ctx.close()
+    c_ref, e_ref = c_ref.cpu().numpy(), e_ref.cpu().numpy()
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        cost = torch.full((w.B,), -1.0, device=gpu)
+        end = torch.full((w.B,), -7, dtype=torch.int64, device=gpu)
+        st = capi.sdtw_forward_noalloc(capi.SDTW_F32, ref.data_ptr(), w.M, qs.data_ptr(),
+                                       offs.data_ptr() if ragged else None, w.B, N, cost.data_ptr(),
+                                       end.data_ptr(), s)
+        assert st == capi.SDTW_OK
+        torch.cuda.synchronize()
+        _same_within_tolerance(c_ref, e_ref, cost.cpu().numpy(), end.cpu().numpy(), w.lengths)
+
+
+def test_noalloc_int8_matches_forward_twice(gpu):
+    w = inputs.paper_i8(B=16, N=200, M=20000, seed=613)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    ctx = SdtwContext(dtype="i8", max_ref_len=w.M, max_batch=w.B, max_query_len=w.N)
+    c_ref, e_ref = ctx.forward(ref, qs)
+    torch.cuda.synchronize()
+    ctx.close()
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        cost = torch.full((w.B,), -1, dtype=torch.int32, device=gpu)
+        end = torch.full((w.B,), -7, dtype=torch.int64, device=gpu)
+        st = capi.sdtw_forward_noalloc(capi.SDTW_I8, ref.data_ptr(), w.M, qs.data_ptr(), None, w.B, w.N,
+                                       cost.data_ptr(), end.data_ptr(), s)
+        assert st == capi.SDTW_OK
+        torch.cuda.synchronize()
+        assert torch.equal(cost.cpu(), c_ref.cpu()) and torch.equal(end.cpu(), e_ref.cpu())
+
+
+def test_noalloc_rejects_batches_over_its_maximum(gpu):
+    z = torch.zeros(8, device=gpu)
+    s = torch.cuda.current_stream().cuda_stream
+    st = capi.sdtw_forward_noalloc(capi.SDTW_F32, z.data_ptr(), 8, z.data_ptr(), None,
+                                   capi.SDTW_NOALLOC_MAX_BATCH + 1, 1, z.data_ptr(), z.data_ptr(), s)
+    assert st == capi.SDTW_E_INVALID
