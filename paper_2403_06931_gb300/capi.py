@@ -44,7 +44,7 @@ class sdtw_config(ctypes.Structure):
         ("seg_width", ctypes.c_int32),
         ("warps_per_query", ctypes.c_int32),
         ("ckpt_stride", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("ckpt_row_stride", ctypes.c_int32),
         ("mem_cap_bytes", ctypes.c_size_t),
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),

@@ -23,7 +23,6 @@ namespace {
 constexpr size_t kDefaultCap = size_t(16) << 30;
 constexpr int kMaxSmem = 227 * 1024;
 constexpr int kI8MaxN = 33000;  // N * 254^2 < 2^31
-constexpr int kBwdStrides[] = {64, 128, 256};
 
 struct DevBuf {
     void* p = nullptr;
@@ -79,7 +78,8 @@ struct sdtw_ctx {
     float* d_rowck = nullptr;  // row checkpoints
     size_t rowck_elems = 0;
     int K_min = 0;        // smallest checkpoint stride the workspace holds for a full chunk
-    int K = 0;            // checkpoint stride in use
+    int K = 0;            // column checkpoint stride in use
+    int R = 0;            // row checkpoint stride in use
     int bwd_chunk = 0;    // queries per backward chunk
     float* d_gyq = nullptr;
     int64_t* d_span = nullptr;
@@ -203,6 +203,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     a.ckpt = ckpt;
     a.rowck = ckpt ? c->d_rowck : nullptr;
     a.K = ckpt ? c->K : 1;
+    a.R = ckpt ? c->R : 2;
     a.nblk = ckpt ? nblk_of(M, c->K) : 0;
     a.ckpt_rows = ckpt ? static_cast<int64_t>(c->bwd_chunk) * c->cfg.max_query_len : 0;
     a.status = c->d_status;
@@ -226,44 +227,57 @@ sdtw_status alloc_backward(sdtw_ctx* c)
     const sdtw_config& f = c->cfg;
     const int64_t M = f.max_ref_len;
     const int64_t N = f.max_query_len;
-    int Ks[3];
-    int nK = 0;
-    if (f.ckpt_stride > 0) {
-        if (!sdtw::bwd_stride_supported(f.ckpt_stride)) return SDTW_E_INVALID;
-        Ks[nK++] = f.ckpt_stride;
-    } else {
-        for (int k : kBwdStrides) Ks[nK++] = k;
+    // (column stride K, row stride R) candidates, most preferred first: tiles
+    // wider than tall suit paths that stretch along the reference
+    int cand[6][2] = {{256, 64}, {256, 128}, {256, 256}, {128, 256}, {64, 256}, {0, 0}};
+    int ncand = 5;
+    if (f.ckpt_stride > 0 || f.ckpt_row_stride > 0) {
+        const int K = f.ckpt_stride > 0 ? f.ckpt_stride : 256;
+        const int R = f.ckpt_row_stride > 0 ? f.ckpt_row_stride : 64;
+        if (!sdtw::bwd_stride_supported(K) || !sdtw::bwd_row_stride_supported(R)) return SDTW_E_INVALID;
+        cand[0][0] = K;
+        cand[0][1] = R;
+        ncand = 1;
     }
     // cost/end scratch for the forward re-run is sized by max_batch, not by the chunk
     const size_t fixed = c->ws_bytes + 12 * static_cast<size_t>(f.max_batch);
-    for (int i = 0; i < nK; ++i) {
-        const int K = Ks[i];
+    int best = -1;
+    int64_t best_fit = 0;
+    for (int i = 0; i < ncand; ++i) {
         // per query: column and row checkpoints, gradient row M floats, span
-        const size_t per_q = 4 * sdtw::ckpt_floats_per_query(N, M, K) + 4 * static_cast<size_t>(M) + 32;
+        const size_t per_q = 4 * sdtw::ckpt_floats_per_query(N, M, cand[i][0], cand[i][1]) +
+                             4 * static_cast<size_t>(M) + 32;
         if (fixed + per_q > c->cap) continue;
         const int64_t fit = static_cast<int64_t>((c->cap - fixed) / per_q);
-        const int chunk = static_cast<int>(std::min<int64_t>(fit, f.max_batch));
-        c->K_min = K;
-        c->K = f.ckpt_stride > 0 ? f.ckpt_stride : 256;
-        c->bwd_chunk = chunk;
-        c->ckpt_elems = static_cast<size_t>(N) * nblk_of(M, K) * chunk;
-        c->rowck_elems = static_cast<size_t>(static_cast<int64_t>(chunk) * N / K) * static_cast<size_t>(M);
-        sdtw_status s;
-        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_ckpt), 4 * std::max<size_t>(c->ckpt_elems, 1))) != SDTW_OK)
-            return s;
-        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_rowck), 4 * std::max<size_t>(c->rowck_elems, 1))) !=
-            SDTW_OK)
-            return s;
-        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_gyq), 4 * static_cast<size_t>(M) * chunk)) != SDTW_OK)
-            return s;
-        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_span), 16 * static_cast<size_t>(chunk))) != SDTW_OK)
-            return s;
-        if ((s = dev_alloc(c, &c->d_cost_tmp, 4 * static_cast<size_t>(f.max_batch))) != SDTW_OK) return s;
-        if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_end_tmp), 8 * static_cast<size_t>(f.max_batch))) != SDTW_OK)
-            return s;
-        return SDTW_OK;
+        if (fit > best_fit) {
+            best = i;
+            best_fit = fit;
+        }
+        if (fit >= f.max_batch) {
+            best = i;
+            break;
+        }
     }
-    return SDTW_E_NOMEM;
+    if (best < 0) return SDTW_E_NOMEM;
+    const int K = cand[best][0], R = cand[best][1];
+    const int chunk = static_cast<int>(std::min<int64_t>(best_fit >= f.max_batch ? f.max_batch : best_fit, f.max_batch));
+    c->K = K;
+    c->R = R;
+    c->K_min = K;
+    c->bwd_chunk = chunk;
+    c->ckpt_elems = static_cast<size_t>(N) * nblk_of(M, K) * chunk;
+    c->rowck_elems = static_cast<size_t>(static_cast<int64_t>(chunk) * N / R) * static_cast<size_t>(M);
+    sdtw_status s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_ckpt), 4 * std::max<size_t>(c->ckpt_elems, 1))) != SDTW_OK)
+        return s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_rowck), 4 * std::max<size_t>(c->rowck_elems, 1))) != SDTW_OK)
+        return s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_gyq), 4 * static_cast<size_t>(M) * chunk)) != SDTW_OK) return s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_span), 16 * static_cast<size_t>(chunk))) != SDTW_OK) return s;
+    if ((s = dev_alloc(c, &c->d_cost_tmp, 4 * static_cast<size_t>(f.max_batch))) != SDTW_OK) return s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_end_tmp), 8 * static_cast<size_t>(f.max_batch))) != SDTW_OK)
+        return s;
+    return SDTW_OK;
 }
 
 void free_all(sdtw_ctx* c)
@@ -393,7 +407,7 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
         ctx->key.M = M;
         ctx->key.B = B;
         ctx->key.N = N;
-        ctx->key.K = ctx->K;
+        ctx->key.K = ctx->K * 1000 + ctx->R;
         ctx->key.valid = true;
     }
     return s;
@@ -410,7 +424,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
     if (s != SDTW_OK) return s;
     if (B > 0 && (!grad_queries || !grad_ref)) return SDTW_E_INVALID;
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
-    if (sdtw::bwd_smem_bytes(N, ctx->K) > kMaxSmem) return SDTW_E_UNSUPPORTED;
+    if (sdtw::bwd_smem_bytes(N, ctx->K, ctx->R) > kMaxSmem) return SDTW_E_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (B == 0) {
@@ -418,7 +432,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         if ((e = cudaMemsetAsync(grad_ref, 0, 4 * static_cast<size_t>(M), st)) != cudaSuccess) return cuda_fail(ctx, e);
         return SDTW_OK;
     }
-    const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N, ctx->K);
+    const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N, ctx->K * 1000 + ctx->R);
     const int chunk = ctx->bwd_chunk;
     for (int q0 = 0; q0 < B; q0 += chunk) {
         const int nq = std::min(chunk, B - q0);
@@ -443,6 +457,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         a.ckpt = ctx->d_ckpt;
         a.rowck = ctx->d_rowck;
         a.K = ctx->K;
+        a.R = ctx->R;
         a.nblk = nblk_of(M, ctx->K);
         a.ckpt_rows = static_cast<int64_t>(ctx->bwd_chunk) * ctx->cfg.max_query_len;
         a.gyq = ctx->d_gyq;

@@ -47,8 +47,8 @@
 //
 // Optional checkpoints for the backward pass, taken as the wavefront passes:
 // a thread whose strip ends at a multiple of K stores that column's absolute D
-// value for every row, and every thread stores its strip of every K-th row
-// (coalesced across the chain).  The backward recomputes K x K tiles from them.
+// value for every row, and every thread stores its strip of every R-th row
+// (coalesced across the chain).  The backward recomputes R x K tiles from them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -210,7 +210,7 @@ fwd_chain_kernel(const FwdArgs a)
         }
         V diag = Md::zero();
         float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
-        float* rck = a.rowck ? a.rowck + ((start - first_start) / a.K) * a.M : nullptr;
+        float* rck = a.rowck ? a.rowck + ((start - first_start) / a.R) * a.M : nullptr;
         V best = INF;
         int best_col = INT_MAX;
         int p = -lag;   // row pair of this thread's tile in sweep s (negative: not started)
@@ -289,8 +289,8 @@ fwd_chain_kernel(const FwdArgs a)
                         ck[2 * p] = static_cast<float>(A[W - 1]) + B;
                         ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
                     }
-                    if (rck && ((2 * p + 2) & (a.K - 1)) == 0) {
-                        float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.K - 1) * a.M + base;
+                    if (rck && ((2 * p + 2) & (a.R - 1)) == 0) {
+                        float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.R - 1) * a.M + base;
 #pragma unroll
                         for (int k = 0; k < W; ++k)
                             if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;
@@ -380,8 +380,8 @@ fwd_chain_kernel(const FwdArgs a)
                             ck[2 * p] = static_cast<float>(A[W - 1]) + B;
                             if (2 * p + 1 < n) ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
                         }
-                        if (rck && ((2 * p + 2) & (a.K - 1)) == 0 && 2 * p + 1 < n) {
-                            float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.K - 1) * a.M + base;
+                        if (rck && ((2 * p + 2) & (a.R - 1)) == 0 && 2 * p + 1 < n) {
+                            float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.R - 1) * a.M + base;
 #pragma unroll
                             for (int k = 0; k < W; ++k)
                                 if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;

@@ -40,11 +40,12 @@ struct FwdArgs {
     // Checkpoints for the backward pass (nullptr: none), absolute D values:
     //   ckpt   every K-th column: query q at (start_q - start_q0) * nblk, block b
     //          (column (b+1)K-1) at b * n_q, one value per row;
-    //   rowck  every K-th row: query q at floor((start_q - start_q0) / K) * M,
-    //          stored row m (row (m+1)K-1) at m * M, one value per column.
+    //   rowck  every R-th row: query q at floor((start_q - start_q0) / R) * M,
+    //          stored row m (row (m+1)R-1) at m * M, one value per column.
     float* ckpt;
     float* rowck;
-    int32_t K;    // checkpoint stride (rows and columns); multiple of the segment width
+    int32_t K;    // column checkpoint stride; a multiple of the segment width
+    int32_t R;    // row checkpoint stride; a power of two
     int64_t nblk; // floor(M / K)
     int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
     int* status;
@@ -84,7 +85,8 @@ struct BwdArgs {
     int32_t* path;
     const float* ckpt;   // column checkpoints of queries q0 .. q0+B-1 (layout as FwdArgs)
     const float* rowck;  // row checkpoints (layout as FwdArgs)
-    int32_t K;           // tile side: checkpoint stride in rows and columns
+    int32_t K;           // tile columns: the column checkpoint stride
+    int32_t R;           // tile rows: the row checkpoint stride
     int64_t nblk;
     int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
@@ -94,8 +96,9 @@ struct BwdArgs {
 
 // Backward launches (sdtw_backward.cu).
 bool bwd_stride_supported(int K);
-int bwd_smem_bytes(int N, int K);
-size_t ckpt_floats_per_query(int64_t N, int64_t M, int K);
+int bwd_smem_bytes(int N, int K, int R);
+size_t ckpt_floats_per_query(int64_t N, int64_t M, int K, int R);
+bool bwd_row_stride_supported(int R);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);

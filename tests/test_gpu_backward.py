@@ -127,11 +127,12 @@ def test_walkback_tie_rule_on_many_queries(gpu):
     assert same >= 5 and matched >= 0.5 * total
 
 
-@pytest.mark.parametrize("B,N,M,K", [(4, 50, 700, 64), (3, 300, 2000, 128), (2, 129, 5000, 256),
-                                     (3, 1, 300, 64), (2, 40, 1, 64), (2, 700, 600, 128)])
-def test_backward_shapes(gpu, B, N, M, K):
+@pytest.mark.parametrize("B,N,M,K,R", [(4, 50, 700, 64, 32), (3, 300, 2000, 128, 64), (2, 129, 5000, 256, 64),
+                                       (3, 1, 300, 64, 256), (2, 40, 1, 64, 32), (2, 700, 600, 128, 128),
+                                       (2, 600, 3000, 256, 256), (3, 257, 1100, 256, 32)])
+def test_backward_shapes(gpu, B, N, M, K, R):
     w = inputs.tiny(B=B, N=N, M=M, seed=500 + B + N + M)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=K)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=K, ckpt_row_stride=R)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     gy_sum = check_validity(w, cost, end, gq, gr, path, g, range(B), oc)
     assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
@@ -141,7 +142,7 @@ def test_backward_long_vertical_runs_cross_windows(gpu):
     # a query far longer than the reference forces long vertical runs, so the
     # walk climbs many rows inside one block (several direction-code windows)
     w = inputs.tiny(B=2, N=2500, M=300, seed=61)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64, ckpt_row_stride=32)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
@@ -156,12 +157,12 @@ def test_backward_ragged(gpu):
 
 def test_chunked_and_recomputed_backward_are_identical(gpu):
     w = inputs.tiny(B=9, N=200, M=4000, seed=81)
-    a = run_bwd(gpu, w, keep=True)                          # checkpoints from the forward
-    b = run_bwd(gpu, w, keep=False)                         # backward re-runs the forward
-    # per query at the smallest stride (64): a column every 64 columns, a row
-    # every 64 rows, one gradient row, span
-    per_q = 4 * (200 * (4000 // 64) + (200 // 64) * 4000) + 4 * 4000 + 32
-    c = run_bwd(gpu, w, keep=False, mem_cap_bytes=3 * per_q + 200_000)   # forces chunks of queries
+    st = dict(ckpt_stride=256, ckpt_row_stride=64)
+    a = run_bwd(gpu, w, keep=True, **st)                          # checkpoints from the forward
+    b = run_bwd(gpu, w, keep=False, **st)                         # backward re-runs the forward
+    # per query: a column every 256 columns, a row every 64 rows, one gradient row, span
+    per_q = 4 * (200 * (4000 // 256) + (200 // 64) * 4000) + 4 * 4000 + 32
+    c = run_bwd(gpu, w, keep=False, mem_cap_bytes=4 * per_q + 20_000, **st)   # forces chunks of 4 queries
     for u, v in ((a, b), (a, c)):
         for k in range(5):
             assert np.array_equal(u[k], v[k])
