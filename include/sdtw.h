@@ -78,7 +78,7 @@ typedef struct sdtw_config {
     int32_t seg_width;           /* reference columns per thread (the paper's segment width); 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
     int32_t ckpt_stride;         /* columns between backward column checkpoints (64, 128, 256); 0 = chosen under mem_cap_bytes */
-    int32_t ckpt_row_stride;     /* rows between backward row checkpoints (32, 64, 128, 256); 0 = chosen under mem_cap_bytes */
+    int32_t ckpt_row_stride;     /* rows between backward row checkpoints (64, 128, 256); 0 = chosen under mem_cap_bytes */
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
     uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
     uint32_t flags;              /* SDTW_FLAG_* */

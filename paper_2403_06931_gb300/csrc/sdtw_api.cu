@@ -156,7 +156,7 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
         while (p.P > 1 && static_cast<int64_t>(32) * (p.P / 2) * p.W >= M) p.P /= 2;
     if (ckpt && c->K % p.W != 0) p.W = 16;
     p.block = 32 * p.P;
-    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P);
+    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, ckpt ? c->K : 0);
     p.persistent = ragged;
     if (p.persistent) {
         int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem);
@@ -590,7 +590,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
             p.W = W;
             p.P = P;
             p.block = 32 * P;
-            p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P);
+            p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, ckpt ? ctx->K : 0);
             if (p.smem > kMaxSmem) continue;
             if (p.persistent) {
                 int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem);
@@ -604,7 +604,8 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
             float ms = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
-                s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, nullptr, 0, B);
+                s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, ckpt ? ctx->d_ckpt : nullptr,
+                                0, B);
                 cudaEventRecord(e1, st);
                 if (s != SDTW_OK) break;
                 if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -289,7 +289,9 @@ cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 
 bool bwd_stride_supported(int K) { return K == 64 || K == 128 || K == 256; }
 
-bool bwd_row_stride_supported(int R) { return R == 32 || R == 64 || R == 128 || R == 256; }
+// at least 64: the forward stages a checkpoint row per warp and needs the
+// 32 lanes' captures of one row to finish before lane 0 reaches the next
+bool bwd_row_stride_supported(int R) { return R == 64 || R == 128 || R == 256; }
 
 int bwd_smem_bytes(int N, int K, int R)
 {

@@ -138,6 +138,12 @@ fwd_chain_kernel(const FwdArgs a)
     V* xs = reinterpret_cast<V*>(colbuf + Npad / 2);       // [Npad]    query samples (zero padded)
     V* red_v = xs + Npad;                                  // [P]       reduction scratch
     int* red_i = reinterpret_cast<int*>(red_v + P);        // [P]
+    // checkpoint staging (only with checkpoints): each warp gathers its 32 strips
+    // of a checkpoint row, and its checkpoint lanes' column values of a chunk,
+    // so that both leave as contiguous 128-byte lines
+    const int nslot = a.ckpt ? 32 * W / a.K : 0;           // checkpoint lanes per warp
+    float* rstage = reinterpret_cast<float*>(red_i + P) + warp * 32 * W;        // [P][32][W]
+    float* cstage = reinterpret_cast<float*>(red_i + P) + P * 32 * W + warp * nslot * 32;  // [P][nslot][32]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
@@ -243,6 +249,8 @@ fwd_chain_kernel(const FwdArgs a)
             if (fast) {
                 float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
                 if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
+                const int p_start = p;
+                float* cslot = ck ? cstage + (((lane + 1) * W) / a.K - 1) * 32 : nullptr;
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
@@ -285,17 +293,40 @@ fwd_chain_kernel(const FwdArgs a)
                         else
                             colbuf[p] = e;
                     }
-                    if (ck) {
-                        ck[2 * p] = static_cast<float>(A[W - 1]) + B;
-                        ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
+                    if (cslot) {
+                        cslot[2 * u] = static_cast<float>(A[W - 1]) + B;
+                        cslot[2 * u + 1] = static_cast<float>(prev[W - 1]) + B;
                     }
-                    if (rck && ((2 * p + 2) & (a.R - 1)) == 0) {
-                        float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.R - 1) * a.M + base;
+                    if (rck) {
+                        if (((2 * p + 2) & (a.R - 1)) == 0) {
 #pragma unroll
-                        for (int k = 0; k < W; ++k)
-                            if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;
+                            for (int k = 0; k < W; ++k) rstage[lane * W + k] = static_cast<float>(prev[k]) + B;
+                        }
+                        // the warp's lanes reach a checkpoint row on consecutive
+                        // steps; once lane 31 has staged it, write the whole row
+                        const int p31 = p + lane - 31;
+                        if (((2 * p31 + 2) & (a.R - 1)) == 0) {
+                            __syncwarp();
+                            const int col0 = s * S + warp * 32 * W;
+                            float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
+                            for (int e = lane; e < 32 * W; e += 32)
+                                if (col0 + e < M) dst[e] = rstage[e];
+                            __syncwarp();
+                        }
                     }
                     ++p;
+                }
+                if (nslot) {
+                    // the chunk's column checkpoints: one 128-byte line per checkpoint lane
+                    __syncwarp();
+                    float* dstl = ck ? ck + 2 * p_start : nullptr;
+                    for (int j = 0; j < nslot; ++j) {
+                        const int src = ((j + 1) * a.K) / W - 1;
+                        float* d = reinterpret_cast<float*>(__shfl_sync(
+                            0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
+                        if (d) d[lane] = cstage[j * 32 + lane];
+                    }
+                    __syncwarp();
                 }
             } else {
 #pragma unroll 1
@@ -306,6 +337,7 @@ fwd_chain_kernel(const FwdArgs a)
                     float rb = 0.f;
                     if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
                     const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(npairs) && s < nsw;
+                    bool rhit = false;
                     if (lane == 0) {
                         if (warp > 0) {
                             const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
@@ -381,11 +413,25 @@ fwd_chain_kernel(const FwdArgs a)
                             if (2 * p + 1 < n) ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
                         }
                         if (rck && ((2 * p + 2) & (a.R - 1)) == 0 && 2 * p + 1 < n) {
-                            float* dst = rck + static_cast<int64_t>((2 * p + 2) / a.R - 1) * a.M + base;
+                            rhit = true;
 #pragma unroll
-                            for (int k = 0; k < W; ++k)
-                                if (base + k < M) dst[k] = static_cast<float>(prev[k]) + B;
+                            for (int k = 0; k < W; ++k) rstage[lane * W + k] = static_cast<float>(prev[k]) + B;
                         }
+                    }
+                    if (rck) {
+                        // write a staged checkpoint row once lane 31 has staged it
+                        // (lanes may straddle a sweep here: use lane 31's sweep and row)
+                        if (__ballot_sync(0xffffffffu, rhit) & 0x80000000u) {
+                            __syncwarp();
+                            const int s31 = __shfl_sync(0xffffffffu, s, 31);
+                            const int p31 = __shfl_sync(0xffffffffu, p, 31);
+                            const int col0 = s31 * S + warp * 32 * W;
+                            float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
+                            for (int e = lane; e < 32 * W; e += 32)
+                                if (col0 + e < M) dst[e] = rstage[e];
+                            __syncwarp();
+                        }
+                        rhit = false;
                     }
                     if (++p == Pp) {
                         p = 0;
@@ -494,12 +540,16 @@ int occupancy_t(int W, int block, int smem)
 
 bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 12 || W == 16 || W == 24 || W == 32; }
 
-int fwd_smem_bytes(sdtw_dtype, int N, int P)
+int fwd_smem_bytes(sdtw_dtype, int N, int P, int W, int K)
 {
     // ring [P][kRing] and column buffer [Npad/2] of 16-byte edges, query samples
-    // [Npad] and the reduction (value, index)[P], 4-byte elements
+    // [Npad] and the reduction (value, index)[P], 4-byte elements; with
+    // checkpoints (K > 0) the row staging [P][32][W] and column staging
+    // [P][32W/K][32] floats
     const int npad = (N + 1) & ~1;
-    return 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
+    int bytes = 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
+    if (K > 0) bytes += 4 * P * (32 * W + (32 * W / K) * 32);
+    return bytes;
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P)

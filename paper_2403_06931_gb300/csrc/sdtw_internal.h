@@ -64,7 +64,7 @@ struct FwdPlan {
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P);
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K);
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem);
 int64_t fwd_total_steps(int64_t M, int N, int W, int P);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);

@@ -127,9 +127,9 @@ def test_walkback_tie_rule_on_many_queries(gpu):
     assert same >= 5 and matched >= 0.5 * total
 
 
-@pytest.mark.parametrize("B,N,M,K,R", [(4, 50, 700, 64, 32), (3, 300, 2000, 128, 64), (2, 129, 5000, 256, 64),
-                                       (3, 1, 300, 64, 256), (2, 40, 1, 64, 32), (2, 700, 600, 128, 128),
-                                       (2, 600, 3000, 256, 256), (3, 257, 1100, 256, 32)])
+@pytest.mark.parametrize("B,N,M,K,R", [(4, 50, 700, 64, 64), (3, 300, 2000, 128, 64), (2, 129, 5000, 256, 64),
+                                       (3, 1, 300, 64, 256), (2, 40, 1, 64, 64), (2, 700, 600, 128, 128),
+                                       (2, 600, 3000, 256, 256), (3, 257, 1100, 256, 64)])
 def test_backward_shapes(gpu, B, N, M, K, R):
     w = inputs.tiny(B=B, N=N, M=M, seed=500 + B + N + M)
     cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=K, ckpt_row_stride=R)
@@ -142,7 +142,7 @@ def test_backward_long_vertical_runs_cross_windows(gpu):
     # a query far longer than the reference forces long vertical runs, so the
     # walk climbs many rows inside one block (several direction-code windows)
     w = inputs.tiny(B=2, N=2500, M=300, seed=61)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64, ckpt_row_stride=32)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64, ckpt_row_stride=64)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
