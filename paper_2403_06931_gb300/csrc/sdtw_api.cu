@@ -581,7 +581,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     float best_ms = 1e30f;
     int best_w = 0, best_p = 0;
     const int Ws[] = {8, 12, 16, 24, 32};
-    const int Ps[] = {1, 2, 4, 8, 16};
+    const int Ps[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
     for (int W : Ws) {
         if (ckpt && ctx->K % W != 0) continue;
         for (int P : Ps) {

@@ -106,6 +106,21 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
     }
 }
 
+// Stage a strip of a checkpoint row: the lane's W values relative to its base,
+// with 16-byte stores, and the base (the flush adds it back).  Runs on one
+// lane at a time, so it is kept short.
+template <int W, typename V>
+__device__ __forceinline__ void stage_row(float* slot, const V (&prev)[W], float* base_slot, float B)
+{
+    static_assert(W % 4 == 0, "segment widths are multiples of 4");
+    float4* s4 = reinterpret_cast<float4*>(slot);
+#pragma unroll
+    for (int k = 0; k < W / 4; ++k)
+        s4[k] = make_float4(static_cast<float>(prev[4 * k]), static_cast<float>(prev[4 * k + 1]),
+                            static_cast<float>(prev[4 * k + 2]), static_cast<float>(prev[4 * k + 3]));
+    *base_slot = B;
+}
+
 // Register cap per segment width: the strip's samples and previous row (2W)
 // plus the tile's short-lived values and bookkeeping, leaving room for several
 // CTAs per SM.
@@ -133,17 +148,25 @@ fwd_chain_kernel(const FwdArgs a)
     const int S = blockDim.x * W;
     const int nsw = (M + S - 1) / S;
 
-    E* ring = reinterpret_cast<E*>(smem_raw);              // [P][kRing] warp-to-warp ring
-    E* colbuf = ring + P * kRing;                          // [Npad/2]  sweep boundary column
-    V* xs = reinterpret_cast<V*>(colbuf + Npad / 2);       // [Npad]    query samples (zero padded)
-    V* red_v = xs + Npad;                                  // [P]       reduction scratch
-    int* red_i = reinterpret_cast<int*>(red_v + P);        // [P]
-    // checkpoint staging (only with checkpoints): each warp gathers its 32 strips
-    // of a checkpoint row, and its checkpoint lanes' column values of a chunk,
-    // so that both leave as contiguous 128-byte lines
+    // shared memory: ring [P][kRing] and column buffer [Npad/2] of 16-byte edges;
+    // with checkpoints, the staging areas (16-byte aligned); query samples
+    // [Npad] (zero padded); reduction scratch (value, index)[P]
     const int nslot = a.ckpt ? 32 * W / a.K : 0;           // checkpoint lanes per warp
-    float* rstage = reinterpret_cast<float*>(red_i + P) + warp * 32 * W;        // [P][32][W]
-    float* cstage = reinterpret_cast<float*>(red_i + P) + P * 32 * W + warp * nslot * 32;  // [P][nslot][32]
+    const int nstage = a.ckpt ? 1 : 0;
+    E* ring = reinterpret_cast<E*>(smem_raw);
+    E* colbuf = ring + P * kRing;
+    // checkpoint staging: each warp gathers its 32 strips of a checkpoint row
+    // (values relative to each lane's base, and the bases) and its checkpoint
+    // lanes' column values of a chunk, so both leave as contiguous 128-byte lines
+    float* rstage_all = reinterpret_cast<float*>(colbuf + Npad / 2);        // [P][32][W]
+    float* rbase_all = rstage_all + nstage * P * 32 * W;                    // [P][32]
+    float* cstage_all = rbase_all + nstage * P * 32;                        // [P][nslot][32]
+    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * 32);              // [Npad]
+    V* red_v = xs + Npad;                                                   // [P]
+    int* red_i = reinterpret_cast<int*>(red_v + P);                         // [P]
+    float* rstage = rstage_all + warp * 32 * W;
+    float* rbase = rbase_all + warp * 32;
+    float* cstage = cstage_all + warp * nslot * 32;
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
@@ -298,10 +321,7 @@ fwd_chain_kernel(const FwdArgs a)
                         cslot[2 * u + 1] = static_cast<float>(prev[W - 1]) + B;
                     }
                     if (rck) {
-                        if (((2 * p + 2) & (a.R - 1)) == 0) {
-#pragma unroll
-                            for (int k = 0; k < W; ++k) rstage[lane * W + k] = static_cast<float>(prev[k]) + B;
-                        }
+                        if (((2 * p + 2) & (a.R - 1)) == 0) stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
                         // the warp's lanes reach a checkpoint row on consecutive
                         // steps; once lane 31 has staged it, write the whole row
                         const int p31 = p + lane - 31;
@@ -310,11 +330,14 @@ fwd_chain_kernel(const FwdArgs a)
                             const int col0 = s * S + warp * 32 * W;
                             float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
                             for (int e = lane; e < 32 * W; e += 32)
-                                if (col0 + e < M) dst[e] = rstage[e];
+                                if (col0 + e < M) dst[e] = rstage[e] + rbase[e / W];
                             __syncwarp();
                         }
                     }
                     ++p;
+                    // a one-warp chain reads and rewrites the column buffer less than
+                    // a chunk apart: order those accesses within the warp
+                    if (P == 1) __syncwarp();
                 }
                 if (nslot) {
                     // the chunk's column checkpoints: one 128-byte line per checkpoint lane
@@ -414,8 +437,7 @@ fwd_chain_kernel(const FwdArgs a)
                         }
                         if (rck && ((2 * p + 2) & (a.R - 1)) == 0 && 2 * p + 1 < n) {
                             rhit = true;
-#pragma unroll
-                            for (int k = 0; k < W; ++k) rstage[lane * W + k] = static_cast<float>(prev[k]) + B;
+                            stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
                         }
                     }
                     if (rck) {
@@ -428,7 +450,7 @@ fwd_chain_kernel(const FwdArgs a)
                             const int col0 = s31 * S + warp * 32 * W;
                             float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
                             for (int e = lane; e < 32 * W; e += 32)
-                                if (col0 + e < M) dst[e] = rstage[e];
+                                if (col0 + e < M) dst[e] = rstage[e] + rbase[e / W];
                             __syncwarp();
                         }
                         rhit = false;
@@ -437,6 +459,7 @@ fwd_chain_kernel(const FwdArgs a)
                         p = 0;
                         ++s;
                     }
+                    if (P == 1) __syncwarp();
                 }
             }
             __syncthreads();
@@ -544,11 +567,11 @@ int fwd_smem_bytes(sdtw_dtype, int N, int P, int W, int K)
 {
     // ring [P][kRing] and column buffer [Npad/2] of 16-byte edges, query samples
     // [Npad] and the reduction (value, index)[P], 4-byte elements; with
-    // checkpoints (K > 0) the row staging [P][32][W] and column staging
-    // [P][32W/K][32] floats
+    // checkpoints (K > 0) the row staging [P][32][W] and its bases [P][32] and
+    // the column staging [P][32W/K][32] floats
     const int npad = (N + 1) & ~1;
     int bytes = 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
-    if (K > 0) bytes += 4 * P * (32 * W + (32 * W / K) * 32);
+    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * 32);
     return bytes;
 }
 

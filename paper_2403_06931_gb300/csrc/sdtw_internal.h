@@ -14,8 +14,8 @@ namespace sdtw {
 // consecutive warps of the chain.  A value crosses from warp w-1 to warp w
 // kChunk+1 steps after it was written, so a barrier always lies between the
 // write and the read; the ring must hold more than 2*kChunk values.
-constexpr int kChunk = 16;
-constexpr int kRing = 64;
+constexpr int kChunk = 32;
+constexpr int kRing = 128;
 static_assert(kRing >= 2 * kChunk + 2, "ring too small for the chunk");
 static_assert((kRing & (kRing - 1)) == 0, "ring size must be a power of two");
 

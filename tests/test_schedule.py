@@ -27,8 +27,8 @@ import pytest
 
 from paper_2403_06931_gb300 import inputs
 
-K_CHUNK = 16   # csrc/sdtw_internal.h kChunk
-K_RING = 64    # csrc/sdtw_internal.h kRing
+K_CHUNK = 32   # csrc/sdtw_internal.h kChunk
+K_RING = 128   # csrc/sdtw_internal.h kRing
 
 
 def simulate_forward(x, y, P, W, K=None):
@@ -141,7 +141,12 @@ def simulate_forward(x, y, P, W, K=None):
                     pp = p[l]
                     if col_w[pp] >= 0 and s[l] > 0:
                         assert col_r[pp] > col_w[pp], "column value overwritten before it was read"
-                        assert chunk(col_r[pp]) < chunk(t), "column overwrite race"
+                        if P == 1:
+                            # reader and writer are lanes of one warp: the per-step
+                            # warp synchronisation orders the read before the write
+                            assert col_r[pp] < t, "column overwrite race"
+                        else:
+                            assert chunk(col_r[pp]) < chunk(t), "column overwrite race"
                     col[pp] = edge
                     col_w[pp] = t
             if K:
@@ -165,7 +170,7 @@ CASES = [
     # (P, W, n, M)
     (1, 4, 40, 300),     # one warp, several sweeps, ragged tail
     (2, 4, 41, 600),     # inter-warp ring, odd query shorter than the chain lag (padded period)
-    (2, 2, 260, 700),    # query longer than the chain lag: fast-path chunks
+    (2, 2, 420, 700),    # query longer than the chain lag: fast-path chunks
     (1, 2, 301, 900),    # odd query, one warp, fast-path chunks
     (3, 2, 5, 1000),     # three warps, tiny query
     (2, 4, 1, 333),      # one-row query
@@ -182,7 +187,7 @@ def test_schedule_reproduces_last_row(oracle_mod, P, W, n, M):
     y = rng.standard_normal(M)
     last_row, _, fast = simulate_forward(x, y, P, W)
     c, e, row = oracle_mod.forward(x, y, last_row=True)
-    if n > 200:
+    if n > 300:
         assert fast > 0
     assert not np.isnan(last_row).any()
     assert np.array_equal(last_row, row)
