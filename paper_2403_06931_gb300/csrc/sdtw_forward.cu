@@ -160,13 +160,13 @@ fwd_chain_kernel(const FwdArgs a)
     // lanes' column values of a chunk, so both leave as contiguous 128-byte lines
     float* rstage_all = reinterpret_cast<float*>(colbuf + Npad / 2);        // [P][32][W]
     float* rbase_all = rstage_all + nstage * P * 32 * W;                    // [P][32]
-    float* cstage_all = rbase_all + nstage * P * 32;                        // [P][nslot][32]
-    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * 32);              // [Npad]
+    float* cstage_all = rbase_all + nstage * P * 32;                        // [P][nslot][2*kChunk]
+    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * 2 * kChunk);      // [Npad]
     V* red_v = xs + Npad;                                                   // [P]
     int* red_i = reinterpret_cast<int*>(red_v + P);                         // [P]
     float* rstage = rstage_all + warp * 32 * W;
     float* rbase = rbase_all + warp * 32;
-    float* cstage = cstage_all + warp * nslot * 32;
+    float* cstage = cstage_all + warp * nslot * 2 * kChunk;
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
@@ -273,7 +273,7 @@ fwd_chain_kernel(const FwdArgs a)
                 float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
                 if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
                 const int p_start = p;
-                float* cslot = ck ? cstage + (((lane + 1) * W) / a.K - 1) * 32 : nullptr;
+                float* cslot = ck ? cstage + (((lane + 1) * W) / a.K - 1) * 2 * kChunk : nullptr;
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
@@ -340,14 +340,18 @@ fwd_chain_kernel(const FwdArgs a)
                     if (P == 1) __syncwarp();
                 }
                 if (nslot) {
-                    // the chunk's column checkpoints: one 128-byte line per checkpoint lane
+                    // the chunk's column checkpoints: 2*kChunk consecutive rows per
+                    // checkpoint lane, written as whole 128-byte lines
                     __syncwarp();
                     float* dstl = ck ? ck + 2 * p_start : nullptr;
                     for (int j = 0; j < nslot; ++j) {
                         const int src = ((j + 1) * a.K) / W - 1;
                         float* d = reinterpret_cast<float*>(__shfl_sync(
                             0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
-                        if (d) d[lane] = cstage[j * 32 + lane];
+                        if (d) {
+#pragma unroll
+                            for (int e = lane; e < 2 * kChunk; e += 32) d[e] = cstage[j * 2 * kChunk + e];
+                        }
                     }
                     __syncwarp();
                 }
@@ -568,10 +572,10 @@ int fwd_smem_bytes(sdtw_dtype, int N, int P, int W, int K)
     // ring [P][kRing] and column buffer [Npad/2] of 16-byte edges, query samples
     // [Npad] and the reduction (value, index)[P], 4-byte elements; with
     // checkpoints (K > 0) the row staging [P][32][W] and its bases [P][32] and
-    // the column staging [P][32W/K][32] floats
+    // the column staging [P][32W/K][2*kChunk] floats
     const int npad = (N + 1) & ~1;
     int bytes = 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
-    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * 32);
+    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * 2 * kChunk);
     return bytes;
 }
 

@@ -62,6 +62,8 @@ def check_validity(w, cost, end, gq, gr, path, g, idx, oracle_costs):
         assert oracle.intervals_are_valid(lo, hi, w.M, int(end[q])), q
         pc = oracle.intervals_cost(x, y, lo, hi)
         oc = oracle_costs[k]
+        # the forward that stored the checkpoints returned the right cost
+        assert abs(float(cost[q]) - oc) <= parity.cost_tol(oc, len(x)), (q, float(cost[q]), oc)
         assert abs(pc - oc) <= parity.cost_tol(oc, len(x)), (q, pc, oc)
         gx, gyq = oracle.intervals_gradient(x, y, lo, hi, g=float(g[q]))
         scale = max(np.abs(gx).max(), 1e-12)
