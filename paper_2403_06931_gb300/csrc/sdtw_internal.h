@@ -14,8 +14,11 @@ namespace sdtw {
 // consecutive warps of the chain.  A value crosses from warp w-1 to warp w
 // kChunk+1 steps after it was written, so a barrier always lies between the
 // write and the read; the ring must hold more than 2*kChunk values.
-constexpr int kChunk = 32;
-constexpr int kRing = 128;
+#ifndef SDTW_CHUNK_STEPS
+#define SDTW_CHUNK_STEPS 32
+#endif
+constexpr int kChunk = SDTW_CHUNK_STEPS;
+constexpr int kRing = 4 * kChunk;
 static_assert(kRing >= 2 * kChunk + 2, "ring too small for the chunk");
 static_assert((kRing & (kRing - 1)) == 0, "ring size must be a power of two");
 
