@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SDTW_ABI_VERSION 1
+#define SDTW_ABI_VERSION 2
 
 typedef struct sdtw_ctx sdtw_ctx;
 
@@ -82,7 +82,7 @@ typedef struct sdtw_config {
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
     uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
     uint32_t flags;              /* SDTW_FLAG_* */
-    uint32_t reserved2;
+    int32_t tile_rows;           /* query rows a thread advances per step (2 or 4); 0 = chosen by the library */
 } sdtw_config;
 
 /* Description of how a call of a given shape will run (for reports and tests). */
@@ -97,6 +97,8 @@ typedef struct sdtw_plan {
     int32_t ckpt_stride;     /* K: columns between checkpoints (0 when none are stored); rows: ckpt_row_stride of the config in use */
     int32_t tuned;           /* 1 if chosen by timing candidates, 0 if the default */
     int64_t sweep_cols;      /* reference columns covered by one sweep of the chain */
+    int32_t tile_rows;       /* query rows a thread advances per step */
+    int32_t reserved;
 } sdtw_plan;
 
 /* ABI version this library was built with (SDTW_ABI_VERSION). */
@@ -232,7 +234,7 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
  * all device memory through its own pool, real-time loops that may not touch
  * the allocator after start-up.  It runs the same persistent forward kernel
  * as sdtw_forward with a fixed plan (32 columns per thread, 4 warps per
- * query); its only scratch (work counter, status word, query order) is one
+ * query, 4 query rows per thread per step); its only scratch (work counter, status word, query order) is one
  * fixed-size array in the library's device memory, which every GPU that
  * loads the library keeps until the process exits.
  *   dtype     SDTW_F32 or SDTW_I8; ref, queries, offsets, B, N, M, cost and

@@ -30,7 +30,7 @@ SDTW_FLAG_GRAD = 0x1
 SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 
 
 class sdtw_config(ctypes.Structure):
@@ -48,7 +48,7 @@ class sdtw_config(ctypes.Structure):
         ("mem_cap_bytes", ctypes.c_size_t),
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),
-        ("reserved2", ctypes.c_uint32),
+        ("tile_rows", ctypes.c_int32),
     ]
 
 
@@ -64,6 +64,8 @@ class sdtw_plan(ctypes.Structure):
         ("ckpt_stride", ctypes.c_int32),
         ("tuned", ctypes.c_int32),
         ("sweep_cols", ctypes.c_int64),
+        ("tile_rows", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):

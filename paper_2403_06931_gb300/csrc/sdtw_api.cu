@@ -90,7 +90,7 @@ struct sdtw_ctx {
     // host-call staging
     DevBuf st_ref, st_q, st_off, st_cost, st_end, st_gc, st_gq, st_gr, st_path;
 
-    std::map<TuneKey, std::pair<int, int>> tuned;  // -> (W, P)
+    std::map<TuneKey, std::tuple<int, int, int>> tuned;  // -> (W, P, RT)
 };
 
 namespace {
@@ -144,22 +144,24 @@ int64_t nblk_of(int64_t M, int K) { return K > 0 ? M / K : 0; }
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
     FwdPlan p;
-    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 16;
-    p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 8;
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 32;
+    p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
+    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
-    if (it != c->tuned.end() && c->cfg.seg_width <= 0 && c->cfg.warps_per_query <= 0) {
-        p.W = it->second.first;
-        p.P = it->second.second;
+    if (it != c->tuned.end()) {
+        if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
+        if (c->cfg.warps_per_query <= 0) p.P = std::get<1>(it->second);
+        if (c->cfg.tile_rows <= 0) p.RT = std::get<2>(it->second);
     }
     // a short reference needs fewer threads per query (unless the caller fixed P)
     if (c->cfg.warps_per_query <= 0)
         while (p.P > 1 && static_cast<int64_t>(32) * (p.P / 2) * p.W >= M) p.P /= 2;
     if (ckpt && c->K % p.W != 0) p.W = 16;
     p.block = 32 * p.P;
-    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, ckpt ? c->K : 0);
+    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, ckpt ? c->K : 0, p.RT);
     p.persistent = ragged;
     if (p.persistent) {
-        int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem);
+        int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
         p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
     } else {
         p.grid = B;
@@ -186,7 +188,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     const bool ragged = offsets != nullptr;
     FwdPlan p = force ? *force : default_fwd_plan(c, nq, N, M, ragged, ckpt != nullptr);
     if (p.smem > kMaxSmem) return SDTW_E_UNSUPPORTED;
-    if (sdtw::fwd_total_steps(M, N, p.W, p.P) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
+    if (sdtw::fwd_total_steps(M, N, p.W, p.P, p.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (p.persistent) p.grid = std::min(p.grid, nq);
     else p.grid = nq;
     FwdArgs a{};
@@ -346,6 +348,7 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & (SDTW_FLAG_GRAD | SDTW_FLAG_KEEP_CHECKPOINTS)) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
+    if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
     if (cfg->dtype == SDTW_I8 && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
 
@@ -579,63 +582,64 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
     float best_ms = 1e30f;
-    int best_w = 0, best_p = 0;
-    const int Ws[] = {8, 12, 16, 24, 32};
+    int best_w = 0, best_p = 0, best_rt = 0;
+    const int Ws[] = {8, 16, 24, 32};
     const int Ps[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
-    for (int W : Ws) {
-        if (ckpt && ctx->K % W != 0) continue;
-        for (int P : Ps) {
-            if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
-            FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
-            p.W = W;
-            p.P = P;
-            p.block = 32 * P;
-            p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, ckpt ? ctx->K : 0);
-            if (p.smem > kMaxSmem) continue;
-            if (p.persistent) {
-                int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem);
+    const int RTs[] = {2, 4};
+    for (int RT : RTs) {
+        for (int W : Ws) {
+            if (ckpt && ctx->K % W != 0) continue;
+            for (int P : Ps) {
+                if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
+                FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
+                p.W = W;
+                p.P = P;
+                p.RT = RT;
+                p.block = 32 * P;
+                p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, ckpt ? ctx->K : 0, RT);
+                if (p.smem > kMaxSmem) continue;
+                const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
                 if (per_sm <= 0) continue;
-                p.grid = std::max(1, std::min(B, per_sm * ctx->sm_count));
-            } else {
-                if (sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem) <= 0) continue;
-                p.grid = B;
-            }
-            // one untimed run, then the best of two timed runs
-            float ms = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, st);
-                s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, ckpt ? ctx->d_ckpt : nullptr,
-                                0, B);
-                cudaEventRecord(e1, st);
-                if (s != SDTW_OK) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    s = SDTW_E_CUDA;
-                    break;
+                p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : B;
+                // one untimed run, then the best of two timed runs
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, st);
+                    s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p,
+                                    ckpt ? ctx->d_ckpt : nullptr, 0, B);
+                    cudaEventRecord(e1, st);
+                    if (s != SDTW_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        s = SDTW_E_CUDA;
+                        break;
+                    }
+                    float t = 0;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) ms = std::min(ms, t);
                 }
-                float t = 0;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (rep > 0) ms = std::min(ms, t);
-            }
-            if (s == SDTW_E_UNSUPPORTED) {
-                s = SDTW_OK;
-                continue;
-            }
-            if (s != SDTW_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return s;
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_w = W;
-                best_p = P;
+                if (s == SDTW_E_UNSUPPORTED) {
+                    s = SDTW_OK;
+                    continue;
+                }
+                if (s != SDTW_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return s;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_w = W;
+                    best_p = P;
+                    best_rt = RT;
+                }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_w == 0) return SDTW_E_UNSUPPORTED;
-    ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] = {best_w, best_p};
+    ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] =
+        std::make_tuple(best_w, best_p, best_rt);
     ctx->key.valid = false;
     if (plan) return sdtw_get_plan(ctx, B, N, M, ragged ? 1 : 0, 0, plan);
     return SDTW_OK;
@@ -661,6 +665,7 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
                       ? 1
                       : 0;
     plan->sweep_cols = static_cast<int64_t>(32) * p.P * p.W;
+    plan->tile_rows = p.RT;
     return SDTW_OK;
 }
 

@@ -7,23 +7,24 @@
 // Schedule.  The CTA's L = 32*P threads form a chain; thread l owns a strip of
 // W consecutive reference columns (the paper's "segment", Section 5.2) and
 // keeps the strip's reference samples and its latest DP row in registers.  At
-// every step a thread advances its strip by a pair of query rows (a 2 x W
-// register tile), and thread l runs one step behind thread l-1, so one step
-// fills an anti-diagonal of tiles.  Inside the tile, cells (r, k) and
-// (r+1, k-1) are independent, so each thread runs two dependency chains; row r
-// goes to a scratch strip and row r+1 overwrites the previous row one column
-// behind it, so no register has to be moved between steps.  The tile's two
-// right-hand cells travel to the next thread by __shfl_up_sync inside a warp;
-// between warps they go through a small shared-memory ring, and warp w runs
-// kChunk+1 steps further behind warp w-1 so that one CTA barrier every kChunk
-// steps orders every ring write before its read.
+// every step a thread advances its strip by RT query rows (an RT x W register
+// tile, RT = 2 or 4), and thread l runs one step behind thread l-1, so one
+// step fills an anti-diagonal of tiles.  Inside the tile, cell j of row r and
+// cell j-1 of row r+1 are independent, so each thread runs RT dependency
+// chains; the tile's first RT-1 rows go to short-lived scratch registers and
+// its last row overwrites the previous row RT-1 columns behind the first, so
+// no register has to be moved between steps.  The tile's RT right-hand cells
+// travel to the next thread by __shfl_up_sync inside a warp; between warps
+// they go through a small shared-memory ring, and warp w runs kChunk+1 steps
+// further behind warp w-1 so that one CTA barrier every kChunk steps orders
+// every ring write before its read.
 //
 // The chain covers S = L*W columns per sweep.  Sweeps are continuous: when a
-// thread finishes the last row pair of sweep s it starts row pair 0 of sweep
-// s+1 (columns shifted by S) on the next step, and the chain's last thread
-// leaves the sweep's right-hand column in a shared-memory column buffer that
-// the first thread reads one sweep later (the paper's double-buffered column
-// between wavefronts, Section 5.2, kept as one buffer indexed by row pair).
+// thread finishes the last tile of rows of sweep s it starts the first tile of
+// sweep s+1 (columns shifted by S) on the next step, and the chain's last
+// thread leaves the sweep's right-hand column in a shared-memory column buffer
+// that the first thread reads one sweep later (the paper's double-buffered
+// column between wavefronts, Section 5.2, kept as one buffer indexed by tile).
 // Threads never idle between sweeps; only the chain's start and end are
 // ragged.  Chunks in which no thread of a warp starts a sweep or reaches the
 // bottom row run a fast path without per-step bookkeeping.
@@ -45,10 +46,12 @@
 // sender's base and are converted on receipt; a sweep starts from base 0.  The
 // drift falls below 1e-7 and the worst error to ~1.5e-6.
 //
-// Optional checkpoints for the backward pass, taken as the wavefront passes:
-// a thread whose strip ends at a multiple of K stores that column's absolute D
-// value for every row, and every thread stores its strip of every R-th row
-// (coalesced across the chain).  The backward recomputes R x K tiles from them.
+// Optional checkpoints for the backward pass, taken as the wavefront passes
+// (a separate instantiation, so the plain forward carries none of it): a
+// thread whose strip ends at a multiple of K stores that column's absolute D
+// value for every row, and every thread stores its strip of every R-th row.
+// Both are staged in shared memory per warp and leave as whole 128-byte lines.
+// The backward recomputes R x K tiles from them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,54 +64,94 @@
 namespace sdtw {
 namespace {
 
-// The two right-hand cells of one row pair of a strip, with their base.
-template <typename V>
+// The RT right-hand cells of one tile of a strip, with their base.
+template <typename V, int RT>
 struct alignas(16) Edge {
-    V v0, v1;
+    V v[RT];
     float b;
-    int pad;
 };
 
-template <typename V>
-struct Pair2;
+template <typename V, int RT>
+struct VecOf;
 template <>
-struct Pair2<float> { using T = float2; };
+struct VecOf<float, 2> { using T = float2; };
 template <>
-struct Pair2<int32_t> { using T = int2; };
+struct VecOf<float, 4> { using T = float4; };
+template <>
+struct VecOf<int32_t, 2> { using T = int2; };
+template <>
+struct VecOf<int32_t, 4> { using T = int4; };
 
-// One 2 x W tile: rows r (into A) and r+1 (over prev), walking the
-// anti-diagonals of the tile so that the two rows form independent chains.
-//   prev   in: row r-1 of the strip; out: row r+1
-//   A      out: row r (A[W-1] is kept for the next step's send)
-//   diag   D(r-1, c-1);  left0 = D(r, c-1);  left1 = D(r+1, c-1)
-template <typename Md, int W>
-__device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md::V (&A)[W],
-                                          const typename Md::V (&y)[W], typename Md::V x0,
-                                          typename Md::V x1, typename Md::V diag,
-                                          typename Md::V left0, typename Md::V left1)
+// the RT query samples of tile p (xs is 16-byte aligned and zero padded)
+template <int RT, typename V>
+__device__ __forceinline__ void load_x(const V* xs, int p, V (&x)[RT])
+{
+    const auto v = reinterpret_cast<const typename VecOf<V, RT>::T*>(xs)[p];
+    x[0] = v.x;
+    x[1] = v.y;
+    if constexpr (RT == 4) {
+        x[2] = v.z;
+        x[3] = v.w;
+    }
+}
+
+// One RT x W tile, walking its anti-diagonals so that its rows form RT
+// independent chains.
+//   prev   in: the strip's previous row; out: the tile's last row
+//   A      out: the tile's other rows (only A[r][W-1] outlives the step)
+//   diag   D of the row above the tile in the column left of the strip
+//   left   D of each tile row in the column left of the strip
+// With BOT, the values of tile row bot_row (relative to base B) update the
+// running bottom-row minimum as they are produced.
+template <typename Md, int W, int RT, bool BOT>
+__device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md::V (&A)[RT - 1][W],
+                                          const typename Md::V (&y)[W], const typename Md::V (&x)[RT],
+                                          typename Md::V diag, const typename Md::V (&left)[RT], int bot_row,
+                                          float B, int base, int M, typename Md::V& best, int& best_col)
 {
     using V = typename Md::V;
 #pragma unroll
-    for (int k = 0; k <= W; ++k) {
-        if (k < W) {
-            const V up = prev[k];
-            const V dg = k == 0 ? diag : prev[k - 1];
-            const V lf = k == 0 ? left0 : A[k - 1];
-            A[k] = Md::cell(x0, y[k], up, dg, lf);
-        }
-        if (k >= 1) {
-            const int j = k - 1;
-            const V up = A[j];
-            const V dg = j == 0 ? left0 : A[j - 1];
-            const V lf = j == 0 ? left1 : prev[j - 1];
-            prev[j] = Md::cell(x1, y[j], up, dg, lf);
+    for (int k = 0; k < W + RT - 1; ++k) {
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) {
+            const int j = k - rr;
+            if (j < 0 || j >= W) continue;
+            V up, dg, lf;
+            if (rr == 0) {
+                up = prev[j];
+                dg = j == 0 ? diag : prev[j - 1];
+            } else {
+                up = A[rr - 1][j];
+                dg = j == 0 ? left[rr - 1] : A[rr - 1][j - 1];
+            }
+            if (j == 0)
+                lf = left[rr];
+            else if (rr == RT - 1)
+                lf = prev[j - 1];
+            else
+                lf = A[rr][j - 1];
+            const V nv = Md::cell(x[rr], y[j], up, dg, lf);
+            if (rr == RT - 1)
+                prev[j] = nv;
+            else
+                A[rr][j] = nv;
+            if constexpr (BOT) {
+                if (rr == bot_row) {
+                    V v = nv;
+                    if constexpr (Md::kRebase) v = nv + B;
+                    if (base + j < M && v < best) {
+                        best = v;
+                        best_col = base + j;
+                    }
+                }
+            }
         }
     }
 }
 
 // Stage a strip of a checkpoint row: the lane's W values relative to its base,
-// with 16-byte stores, and the base (the flush adds it back).  Runs on one
-// lane at a time, so it is kept short.
+// with 16-byte stores, and the base (the flush adds it back).  Runs on a few
+// lanes at a time, so it is kept short.
 template <int W, typename V>
 __device__ __forceinline__ void stage_row(float* slot, const V (&prev)[W], float* base_slot, float B)
 {
@@ -121,20 +164,25 @@ __device__ __forceinline__ void stage_row(float* slot, const V (&prev)[W], float
     *base_slot = B;
 }
 
-// Register cap per segment width: the strip's samples and previous row (2W)
-// plus the tile's short-lived values and bookkeeping, leaving room for several
-// CTAs per SM.
-template <int W>
-constexpr int fwd_reg_cap() { return W <= 8 ? 72 : W <= 12 ? 80 : W <= 16 ? 88 : W <= 24 ? 112 : 128; }
+// Register cap per segment width and tile height: the strip's samples and
+// previous row (2W), the tile's short-lived values and bookkeeping, leaving
+// room for several CTAs per SM.
+// (one template argument, W * 8 + RT, as the attribute takes a single expression)
+template <int WRT>
+constexpr int fwd_reg_cap()
+{
+    constexpr int W = WRT / 8, RT = WRT % 8;
+    return W <= 8 ? (RT == 2 ? 72 : 80) : W <= 16 ? (RT == 2 ? 88 : 96) : W <= 24 ? (RT == 2 ? 112 : 120) : 128;
+}
 
-template <typename Tin, int W>
-__global__ void __maxnreg__(fwd_reg_cap<W>())
+template <typename Tin, int W, int RT, bool CKPT>
+__global__ void __maxnreg__(fwd_reg_cap<W * 8 + RT>())
 fwd_chain_kernel(const FwdArgs a)
 {
     using Md = Mode<Tin>;
     using V = typename Md::V;
-    using E = Edge<V>;
-    using V2 = typename Pair2<V>::T;
+    using E = Edge<V, RT>;
+    static_assert(RT == 2 || RT == 4, "tiles of 2 or 4 rows");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_query;
@@ -143,30 +191,28 @@ fwd_chain_kernel(const FwdArgs a)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int N = a.N;
-    const int Npad = (N + 1) & ~1;
+    const int Npad = (N + RT - 1) / RT * RT;
     const int M = static_cast<int>(a.M);
     const int S = blockDim.x * W;
     const int nsw = (M + S - 1) / S;
 
-    // shared memory: ring [P][kRing] and column buffer [Npad/2] of 16-byte edges;
-    // with checkpoints, the staging areas (16-byte aligned); query samples
-    // [Npad] (zero padded); reduction scratch (value, index)[P]
-    const int nslot = a.ckpt ? 32 * W / a.K : 0;           // checkpoint lanes per warp
-    const int nstage = a.ckpt ? 1 : 0;
+    // shared memory: ring [P][kRing] and column buffer [Npad/RT] of edges; with
+    // checkpoints the staging areas; query samples [Npad] (zero padded);
+    // reduction scratch (value, index)[P].  Every part is 16-byte aligned.
+    const int nslot = CKPT ? 32 * W / a.K : 0;  // checkpoint lanes per warp
     E* ring = reinterpret_cast<E*>(smem_raw);
     E* colbuf = ring + P * kRing;
+    float* stage = reinterpret_cast<float*>(colbuf + Npad / RT);
     // checkpoint staging: each warp gathers its 32 strips of a checkpoint row
     // (values relative to each lane's base, and the bases) and its checkpoint
-    // lanes' column values of a chunk, so both leave as contiguous 128-byte lines
-    float* rstage_all = reinterpret_cast<float*>(colbuf + Npad / 2);        // [P][32][W]
-    float* rbase_all = rstage_all + nstage * P * 32 * W;                    // [P][32]
-    float* cstage_all = rbase_all + nstage * P * 32;                        // [P][nslot][2*kChunk]
-    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * 2 * kChunk);      // [Npad]
-    V* red_v = xs + Npad;                                                   // [P]
-    int* red_i = reinterpret_cast<int*>(red_v + P);                         // [P]
-    float* rstage = rstage_all + warp * 32 * W;
-    float* rbase = rbase_all + warp * 32;
-    float* cstage = cstage_all + warp * nslot * 2 * kChunk;
+    // lanes' column values of a chunk, so both leave as contiguous lines
+    float* rstage = stage + warp * 32 * W;                         // [P][32][W]
+    float* rbase = stage + (CKPT ? P * 32 * W : 0) + warp * 32;     // [P][32]
+    float* cstage_all = stage + (CKPT ? P * 32 * (W + 1) : 0);      // [P][nslot][RT*kChunk]
+    float* cstage = cstage_all + warp * nslot * RT * kChunk;
+    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * RT * kChunk);  // [Npad]
+    V* red_v = xs + Npad;                                                // [P]
+    int* red_i = reinterpret_cast<int*>(red_v + P);                      // [P]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
@@ -178,6 +224,10 @@ fwd_chain_kernel(const FwdArgs a)
     const E* ring_in = ring + warp * kRing;
     E* ring_out = ring + (warp + 1) * kRing;
     const V INF = Md::inf();
+    // checkpoint rows: lanes reach a row on consecutive steps and reach the
+    // next one R/RT steps later, so rows are staged and written out per group
+    // of G = min(32, R/RT) lanes
+    const int G = CKPT ? min(32, a.R / RT) : 32;
 
     for (int it = 0;; ++it) {
         int q;
@@ -200,7 +250,7 @@ fwd_chain_kernel(const FwdArgs a)
             const int64_t stop = a.offsets[q + 1];
             const int64_t len = stop - start;
             bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total];
-            if (a.ckpt) bad = bad || start < first_start || (stop - first_start) > a.ckpt_rows;
+            if (CKPT) bad = bad || start < first_start || (stop - first_start) > a.ckpt_rows;
             if (bad) {
                 if (threadIdx.x == 0) atomicOr(a.status, kStatusBadLength);
                 __syncthreads();
@@ -220,32 +270,33 @@ fwd_chain_kernel(const FwdArgs a)
             continue;
         }
 
-        for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = Md::widen(queries[start + i]);
-        if (threadIdx.x == 0 && (n & 1)) xs[n] = Md::zero();  // a dummy row completes the last pair
+        const int nt = (n + RT - 1) / RT;  // tiles of rows per sweep
+        for (int i = threadIdx.x; i < nt * RT; i += blockDim.x)
+            xs[i] = i < n ? Md::widen(queries[start + i]) : Md::zero();  // dummy rows complete the last tile
         __syncthreads();
 
-        const int npairs = (n + 1) >> 1;
-        const int lastp = npairs - 1;                      // the pair holding row n-1
-        const int Pp = max(npairs, lag_last + kChunk);     // sweep period in steps
-        const int total = (nsw - 1) * Pp + npairs + lag_last;
-        const V2* xs2 = reinterpret_cast<const V2*>(xs);
+        const int lastt = nt - 1;                 // the tile holding row n-1
+        const int bot = (n - 1) - RT * lastt;     // ... as its row bot
+        const int Pp = max(nt, lag_last + kChunk);  // sweep period in steps
+        const int total = (nsw - 1) * Pp + nt + lag_last;
 
-        V y[W], prev[W], A[W];
+        V y[W], prev[W], A[RT - 1][W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             y[k] = Md::zero();
             prev[k] = Md::zero();
-            A[k] = Md::zero();
+#pragma unroll
+            for (int rr = 0; rr < RT - 1; ++rr) A[rr][k] = Md::zero();
         }
         V diag = Md::zero();
         float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
-        float* rck = a.rowck ? a.rowck + ((start - first_start) / a.R) * a.M : nullptr;
         V best = INF;
         int best_col = INT_MAX;
-        int p = -lag;   // row pair of this thread's tile in sweep s (negative: not started)
+        int p = -lag;   // tile of this thread's strip in sweep s (negative: not started)
         int s = 0;      // sweep
         int base = threadIdx.x * W;  // first column of the strip in sweep s
         float* ck = nullptr;
+        float* rck = CKPT ? a.rowck + ((start - first_start) / a.R) * a.M : nullptr;
 
         for (int t0 = 0; t0 < total; t0 += kChunk) {
             if constexpr (Md::kRebase) {
@@ -256,7 +307,8 @@ fwd_chain_kernel(const FwdArgs a)
                 const float dl = bn - B;
 #pragma unroll
                 for (int k = 0; k < W; ++k) prev[k] -= dl;
-                A[W - 1] -= dl;
+#pragma unroll
+                for (int rr = 0; rr < RT - 1; ++rr) A[rr][W - 1] -= dl;
                 diag -= dl;
                 B = bn;
             }
@@ -267,70 +319,77 @@ fwd_chain_kernel(const FwdArgs a)
             bool fast = gmin >= 0;
             if (fast) {
                 const int sw = gmin / Pp;
-                fast = gmax / Pp == sw && sw < nsw && gmin - sw * Pp >= 1 && gmax - sw * Pp <= lastp - 1;
+                fast = gmax / Pp == sw && sw < nsw && gmin - sw * Pp >= 1 && gmax - sw * Pp <= lastt - 1;
             }
             if (fast) {
                 float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
                 if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
                 const int p_start = p;
-                float* cslot = ck ? cstage + (((lane + 1) * W) / a.K - 1) * 2 * kChunk : nullptr;
+                float* cslot = (CKPT && ck) ? cstage + (((lane + 1) * W) / a.K - 1) * RT * kChunk : nullptr;
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
-                    V v0 = __shfl_up_sync(0xffffffffu, A[W - 1], 1);
-                    V v1 = __shfl_up_sync(0xffffffffu, prev[W - 1], 1);
+                    V recv[RT];
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr)
+                        recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
                     float dd = dconv;
                     if (lane == 0) {
                         if (warp > 0) {
                             const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
-                            v0 = e.v0;
-                            v1 = e.v1;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
                             dd = e.b - B;
                         } else if (s > 0) {
                             const E e = colbuf[p];
-                            v0 = e.v0;
-                            v1 = e.v1;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
                             dd = e.b - B;
                         } else {
-                            v0 = INF;
-                            v1 = INF;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
                             dd = 0.f;
                         }
                     }
-                    V left0 = v0, left1 = v1;
-                    if constexpr (Md::kRebase) {
-                        left0 = v0 + dd;
-                        left1 = v1 + dd;
+                    V left[RT];
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) {
+                        left[rr] = recv[rr];
+                        if constexpr (Md::kRebase) left[rr] = recv[rr] + dd;
                     }
-                    const V2 xp = xs2[p];
-                    tile_step<Md, W>(prev, A, y, xp.x, xp.y, diag, left0, left1);
-                    diag = left1;
+                    V x[RT];
+                    load_x<RT>(xs, p, x);
+                    tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
+                    diag = left[RT - 1];
                     if (lane == 31) {
                         E e;
-                        e.v0 = A[W - 1];
-                        e.v1 = prev[W - 1];
+#pragma unroll
+                        for (int rr = 0; rr < RT; ++rr) e.v[rr] = rr < RT - 1 ? A[rr][W - 1] : prev[W - 1];
                         e.b = B;
-                        e.pad = 0;
                         if (warp < P - 1)
                             ring_out[t & (kRing - 1)] = e;
                         else
                             colbuf[p] = e;
                     }
-                    if (cslot) {
-                        cslot[2 * u] = static_cast<float>(A[W - 1]) + B;
-                        cslot[2 * u + 1] = static_cast<float>(prev[W - 1]) + B;
-                    }
-                    if (rck) {
-                        if (((2 * p + 2) & (a.R - 1)) == 0) stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
-                        // the warp's lanes reach a checkpoint row on consecutive
-                        // steps; once lane 31 has staged it, write the whole row
-                        const int p31 = p + lane - 31;
-                        if (((2 * p31 + 2) & (a.R - 1)) == 0) {
+                    if constexpr (CKPT) {
+                        if (cslot) {
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr)
+                                cslot[RT * u + rr] = static_cast<float>(rr < RT - 1 ? A[rr][W - 1] : prev[W - 1]) + B;
+                        }
+                        if ((((p + 1) * RT) & (a.R - 1)) == 0) stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
+                        // write out each group of G lanes once its last lane has staged
+                        const int pg = p + lane - (G - 1);  // tile of lane G-1 (same sweep here)
+                        if ((((pg + 1) * RT) & (a.R - 1)) == 0) {
                             __syncwarp();
                             const int col0 = s * S + warp * 32 * W;
-                            float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
-                            for (int e = lane; e < 32 * W; e += 32)
-                                if (col0 + e < M) dst[e] = rstage[e] + rbase[e / W];
+                            for (int e = lane; e < 32 * W; e += 32) {
+                                const int gl = (e / (G * W)) * G + G - 1;  // last lane of e's group
+                                const int pl = p + lane - gl;
+                                const int m = ((pl + 1) * RT) / a.R - 1;
+                                if (col0 + e < M)
+                                    rck[static_cast<int64_t>(m) * a.M + col0 + e] = rstage[e] + rbase[e / W];
+                            }
                             __syncwarp();
                         }
                     }
@@ -339,46 +398,49 @@ fwd_chain_kernel(const FwdArgs a)
                     // a chunk apart: order those accesses within the warp
                     if (P == 1) __syncwarp();
                 }
-                if (nslot) {
-                    // the chunk's column checkpoints: 2*kChunk consecutive rows per
-                    // checkpoint lane, written as whole 128-byte lines
-                    __syncwarp();
-                    float* dstl = ck ? ck + 2 * p_start : nullptr;
-                    for (int j = 0; j < nslot; ++j) {
-                        const int src = ((j + 1) * a.K) / W - 1;
-                        float* d = reinterpret_cast<float*>(__shfl_sync(
-                            0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
-                        if (d) {
-#pragma unroll
-                            for (int e = lane; e < 2 * kChunk; e += 32) d[e] = cstage[j * 2 * kChunk + e];
+                if constexpr (CKPT) {
+                    if (nslot) {
+                        // the chunk's column checkpoints: RT*kChunk consecutive rows
+                        // per checkpoint lane, written as whole lines
+                        __syncwarp();
+                        float* dstl = ck ? ck + RT * p_start : nullptr;
+                        for (int j = 0; j < nslot; ++j) {
+                            const int src = ((j + 1) * a.K) / W - 1;
+                            float* d = reinterpret_cast<float*>(__shfl_sync(
+                                0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
+                            if (d) {
+                                for (int e = lane; e < RT * kChunk; e += 32) d[e] = cstage[j * RT * kChunk + e];
+                            }
                         }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
             } else {
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
-                    V v0 = __shfl_up_sync(0xffffffffu, A[W - 1], 1);
-                    V v1 = __shfl_up_sync(0xffffffffu, prev[W - 1], 1);
+                    V recv[RT];
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr)
+                        recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
                     float rb = 0.f;
                     if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
-                    const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(npairs) && s < nsw;
+                    const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(nt) && s < nsw;
                     bool rhit = false;
                     if (lane == 0) {
                         if (warp > 0) {
                             const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
-                            v0 = e.v0;
-                            v1 = e.v1;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
                             rb = e.b;
                         } else if (act && s > 0) {
                             const E e = colbuf[p];
-                            v0 = e.v0;
-                            v1 = e.v1;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
                             rb = e.b;
                         } else {
-                            v0 = INF;
-                            v1 = INF;
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
                             rb = 0.f;
                         }
                     }
@@ -395,69 +457,68 @@ fwd_chain_kernel(const FwdArgs a)
                             }
                             diag = Md::zero();
                             B = 0.f;
-                            ck = nullptr;
-                            if (a.ckpt) {
+                            if constexpr (CKPT) {
+                                ck = nullptr;
                                 const int edge = base + W;
                                 if (edge % a.K == 0 && edge / a.K <= a.nblk)
                                     ck = a.ckpt + (start - first_start) * a.nblk +
                                          static_cast<int64_t>(edge / a.K - 1) * n;
                             }
                         }
-                        V left0 = v0, left1 = v1;
-                        if constexpr (Md::kRebase) {
-                            const float dd = rb - B;  // into this thread's base
-                            left0 = v0 + dd;
-                            left1 = v1 + dd;
-                        }
-                        const V2 xp = xs2[p];
-                        tile_step<Md, W>(prev, A, y, xp.x, xp.y, diag, left0, left1);
-                        diag = left1;
-                        if (p == lastp) {
-                            // row n-1 is the pair's first row (odd n) or its second
+                        V left[RT];
 #pragma unroll
-                            for (int k = 0; k < W; ++k) {
-                                V v = (n & 1) ? A[k] : prev[k];
-                                if constexpr (Md::kRebase) v = v + B;
-                                if (base + k < M && v < best) {
-                                    best = v;
-                                    best_col = base + k;
-                                }
-                            }
+                        for (int rr = 0; rr < RT; ++rr) {
+                            left[rr] = recv[rr];
+                            if constexpr (Md::kRebase) left[rr] = recv[rr] + (rb - B);  // into this thread's base
                         }
+                        V x[RT];
+                        load_x<RT>(xs, p, x);
+                        tile_step<Md, W, RT, true>(prev, A, y, x, diag, left, p == lastt ? bot : -1, B, base, M,
+                                                   best, best_col);
+                        diag = left[RT - 1];
                         if (lane == 31) {
                             E e;
-                            e.v0 = A[W - 1];
-                            e.v1 = prev[W - 1];
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) e.v[rr] = rr < RT - 1 ? A[rr][W - 1] : prev[W - 1];
                             e.b = B;
-                            e.pad = 0;
                             if (warp < P - 1)
                                 ring_out[t & (kRing - 1)] = e;
                             else
                                 colbuf[p] = e;
                         }
-                        if (ck) {
-                            ck[2 * p] = static_cast<float>(A[W - 1]) + B;
-                            if (2 * p + 1 < n) ck[2 * p + 1] = static_cast<float>(prev[W - 1]) + B;
-                        }
-                        if (rck && ((2 * p + 2) & (a.R - 1)) == 0 && 2 * p + 1 < n) {
-                            rhit = true;
-                            stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
+                        if constexpr (CKPT) {
+                            if (ck) {
+#pragma unroll
+                                for (int rr = 0; rr < RT; ++rr)
+                                    if (RT * p + rr < n)
+                                        ck[RT * p + rr] = static_cast<float>(rr < RT - 1 ? A[rr][W - 1] : prev[W - 1]) + B;
+                            }
+                            if ((((p + 1) * RT) & (a.R - 1)) == 0 && RT * p + RT - 1 < n) {
+                                rhit = true;
+                                stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
+                            }
                         }
                     }
-                    if (rck) {
-                        // write a staged checkpoint row once lane 31 has staged it
-                        // (lanes may straddle a sweep here: use lane 31's sweep and row)
-                        if (__ballot_sync(0xffffffffu, rhit) & 0x80000000u) {
+                    if constexpr (CKPT) {
+                        // write out each group of G lanes whose last lane staged just
+                        // now (lanes may straddle a sweep here: each group uses the
+                        // sweep and tile of its last lane)
+                        const unsigned hits = __ballot_sync(0xffffffffu, rhit);
+                        bool any = false;
+                        for (int g = G - 1; g < 32; g += G) any |= (hits >> g) & 1u;
+                        if (any) {
                             __syncwarp();
-                            const int s31 = __shfl_sync(0xffffffffu, s, 31);
-                            const int p31 = __shfl_sync(0xffffffffu, p, 31);
-                            const int col0 = s31 * S + warp * 32 * W;
-                            float* dst = rck + static_cast<int64_t>((2 * p31 + 2) / a.R - 1) * a.M + col0;
-                            for (int e = lane; e < 32 * W; e += 32)
-                                if (col0 + e < M) dst[e] = rstage[e] + rbase[e / W];
+                            for (int e = lane; e < 32 * W; e += 32) {
+                                const int gl = (e / (G * W)) * G + G - 1;
+                                const int sl = __shfl_sync(0xffffffffu, s, gl);
+                                const int pl = __shfl_sync(0xffffffffu, p, gl);
+                                const int col0 = sl * S + warp * 32 * W;
+                                const int m = ((pl + 1) * RT) / a.R - 1;
+                                if (((hits >> gl) & 1u) && col0 + e < M)
+                                    rck[static_cast<int64_t>(m) * a.M + col0 + e] = rstage[e] + rbase[e / W];
+                            }
                             __syncwarp();
                         }
-                        rhit = false;
                     }
                     if (++p == Pp) {
                         p = 0;
@@ -515,89 +576,96 @@ __global__ void order_by_length_kernel(const int64_t* __restrict__ offsets, int3
     order[rank] = q;
 }
 
-template <typename Tin, int W>
-cudaError_t launch_w(const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
-{
-    auto k = fwd_chain_kernel<Tin, W>;
-    if (plan.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
-        if (e != cudaSuccess) return e;
+template <typename Tin, int W, int RT, bool CKPT>
+struct Inst {
+    static cudaError_t launch(const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
+    {
+        auto k = fwd_chain_kernel<Tin, W, RT, CKPT>;
+        if (plan.smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<plan.grid, plan.block, plan.smem, s>>>(a);
+        return cudaGetLastError();
     }
-    k<<<plan.grid, plan.block, plan.smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename Tin>
-cudaError_t launch_t(const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
-{
-    switch (plan.W) {
-    case 8: return launch_w<Tin, 8>(plan, a, s);
-    case 12: return launch_w<Tin, 12>(plan, a, s);
-    case 16: return launch_w<Tin, 16>(plan, a, s);
-    case 24: return launch_w<Tin, 24>(plan, a, s);
-    case 32: return launch_w<Tin, 32>(plan, a, s);
-    default: return cudaErrorInvalidValue;
+    static int occupancy(int block, int smem)
+    {
+        int n = 0;
+        auto k = fwd_chain_kernel<Tin, W, RT, CKPT>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
+        return n;
     }
-}
+};
 
-template <typename Tin, int W>
-int occupancy_w(int block, int smem)
+// dispatch (dtype, W, RT, checkpoints) to an instantiation; checkpoints exist
+// only in FP32 mode (the backward is FP32 only)
+template <typename F>
+cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 {
-    int n = 0;
-    auto k = fwd_chain_kernel<Tin, W>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
-    return n;
-}
-
-template <typename Tin>
-int occupancy_t(int W, int block, int smem)
-{
-    switch (W) {
-    case 8: return occupancy_w<Tin, 8>(block, smem);
-    case 12: return occupancy_w<Tin, 12>(block, smem);
-    case 16: return occupancy_w<Tin, 16>(block, smem);
-    case 24: return occupancy_w<Tin, 24>(block, smem);
-    case 32: return occupancy_w<Tin, 32>(block, smem);
-    default: return 0;
+#define SDTW_W(Tin, RTv, CK)                                              \
+    switch (W) {                                                          \
+    case 8: return f(Inst<Tin, 8, RTv, CK>{});                            \
+    case 16: return f(Inst<Tin, 16, RTv, CK>{});                          \
+    case 24: return f(Inst<Tin, 24, RTv, CK>{});                          \
+    case 32: return f(Inst<Tin, 32, RTv, CK>{});                          \
+    default: return cudaErrorInvalidValue;                                \
     }
+    if (RT != 2 && RT != 4) return cudaErrorInvalidValue;
+    if (dt == SDTW_I8) {
+        if (ckpt) return cudaErrorInvalidValue;
+        if (RT == 2) { SDTW_W(int8_t, 2, false) } else { SDTW_W(int8_t, 4, false) }
+    }
+    if (ckpt) {
+        if (RT == 2) { SDTW_W(float, 2, true) } else { SDTW_W(float, 4, true) }
+    }
+    if (RT == 2) { SDTW_W(float, 2, false) } else { SDTW_W(float, 4, false) }
+#undef SDTW_W
 }
 
 }  // namespace
 
-bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 12 || W == 16 || W == 24 || W == 32; }
+bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
 
-int fwd_smem_bytes(sdtw_dtype, int N, int P, int W, int K)
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K, int RT)
 {
-    // ring [P][kRing] and column buffer [Npad/2] of 16-byte edges, query samples
-    // [Npad] and the reduction (value, index)[P], 4-byte elements; with
-    // checkpoints (K > 0) the row staging [P][32][W] and its bases [P][32] and
-    // the column staging [P][32W/K][2*kChunk] floats
-    const int npad = (N + 1) & ~1;
-    int bytes = 16 * (P * kRing + npad / 2) + 4 * (npad + 2 * P);
-    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * 2 * kChunk);
+    // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
+    // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
+    // 4-byte elements; with checkpoints (K > 0) the row staging [P][32][W], its
+    // bases [P][32] and the column staging [P][32W/K][RT*kChunk] floats
+    (void)dt;
+    const int npad = (N + RT - 1) / RT * RT;
+    const int esz = RT == 2 ? 16 : 32;
+    int bytes = esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
+    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * RT * kChunk);
     return bytes;
 }
 
-int64_t fwd_total_steps(int64_t M, int N, int W, int P)
+int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
 {
     const int64_t S = static_cast<int64_t>(32) * P * W;
     const int64_t nsw = (M + S - 1) / S;
     const int64_t lag_last = static_cast<int64_t>(P - 1) * (32 + kChunk) + 31;
-    const int64_t npairs = (N + 1) / 2;
-    const int64_t Pp = std::max<int64_t>(npairs, lag_last + kChunk);
-    return (nsw - 1) * Pp + npairs + lag_last;
+    const int64_t nt = (N + RT - 1) / RT;
+    const int64_t Pp = std::max<int64_t>(nt, lag_last + kChunk);
+    return (nsw - 1) * Pp + nt + lag_last;
 }
 
-int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem)
+int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt)
 {
-    return dt == SDTW_I8 ? occupancy_t<int8_t>(W, P * 32, smem) : occupancy_t<float>(W, P * 32, smem);
+    int n = 0;
+    dispatch(dt, W, RT, ckpt, [&](auto inst) {
+        n = decltype(inst)::occupancy(32 * P, smem);
+        return cudaSuccess;
+    });
+    return n;
 }
 
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
 {
     if (plan.grid <= 0) return cudaSuccess;
-    return dt == SDTW_I8 ? launch_t<int8_t>(plan, a, s) : launch_t<float>(plan, a, s);
+    return dispatch(dt, plan.W, plan.RT, a.ckpt != nullptr,
+                    [&](auto inst) { return decltype(inst)::launch(plan, a, s); });
 }
 
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s)

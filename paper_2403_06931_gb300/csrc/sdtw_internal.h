@@ -59,6 +59,7 @@ struct FwdArgs {
 struct FwdPlan {
     int W = 16;          // segment width: reference columns per thread
     int P = 8;           // warps per query chain
+    int RT = 2;          // query rows per thread per step (tile height)
     bool persistent = false;
     int grid = 0;
     int block = 0;
@@ -67,9 +68,9 @@ struct FwdPlan {
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K);
-int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem);
-int64_t fwd_total_steps(int64_t M, int N, int W, int P);
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K, int RT);
+int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt);
+int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s);
 

@@ -68,12 +68,13 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     sdtw::FwdPlan plan;
     plan.W = 32;
     plan.P = 4;
+    plan.RT = 4;
     while (plan.P > 1 && static_cast<int64_t>(32) * (plan.P / 2) * plan.W >= M) plan.P /= 2;
     plan.block = 32 * plan.P;
-    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, 0);
+    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, 0, plan.RT);
     plan.persistent = true;
     if (plan.smem > 227 * 1024) return SDTW_E_UNSUPPORTED;
-    if (sdtw::fwd_total_steps(M, N, plan.W, plan.P) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
+    if (sdtw::fwd_total_steps(M, N, plan.W, plan.P, plan.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
 
     int32_t* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return SDTW_E_CUDA;
@@ -81,7 +82,7 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SDTW_E_CUDA;
-    const int per_sm = sdtw::fwd_max_ctas_per_sm(dtype, plan.W, plan.P, plan.smem);
+    const int per_sm = sdtw::fwd_max_ctas_per_sm(dtype, plan.W, plan.P, plan.smem, plan.RT, false);
     if (per_sm <= 0) return SDTW_E_UNSUPPORTED;
     plan.grid = std::max(1, std::min(B, per_sm * sms));
 

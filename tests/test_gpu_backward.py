@@ -140,6 +140,16 @@ def test_backward_shapes(gpu, B, N, M, K, R):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
 
 
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("W", [8, 16, 32])
+def test_backward_every_tile_height_and_width(gpu, RT, W):
+    # checkpoints taken by every forward variant: rows staged in groups (RT = 4, R = 64)
+    w = inputs.tiny(B=3, N=700, M=9000, seed=400 + RT + W)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=2)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+
+
 def test_backward_long_vertical_runs_cross_windows(gpu):
     # a query far longer than the reference forces long vertical runs, so the
     # walk climbs many rows inside one block (several direction-code windows)

@@ -52,33 +52,36 @@ def test_shapes_fp32(gpu, B, N, M):
     assert parity.check_forward_f32(w.ref, w.query, range(B), cost, end) == []
 
 
-@pytest.mark.parametrize("W", [8, 12, 16, 24, 32])
-@pytest.mark.parametrize("P", [1, 2, 4, 8, 16])
-def test_every_plan_fp32(gpu, W, P):
-    w = inputs.tiny(B=3, N=90, M=6000, seed=77)
-    cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P)
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("W", [8, 16, 24, 32])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 8, 16])
+def test_every_plan_fp32(gpu, W, P, RT):
+    w = inputs.tiny(B=3, N=91, M=6000, seed=77)
+    cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
 
-@pytest.mark.parametrize("W", [8, 12, 16, 24, 32])
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("W", [8, 16, 24, 32])
 @pytest.mark.parametrize("P", [1, 4, 16])
-def test_every_plan_i8_bit_exact(gpu, W, P):
+def test_every_plan_i8_bit_exact(gpu, W, P, RT):
     w = inputs.paper_i8(B=4, N=70, M=5000, seed=78)
-    cost, end = run_fwd(gpu, w.ref, w.queries, dtype="i8", seg_width=W, warps_per_query=P)
+    cost, end = run_fwd(gpu, w.ref, w.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT)
     assert cost.dtype == np.int32
     assert parity.check_forward_i8(w.ref, w.query, range(w.B), cost, end) == []
 
 
-@pytest.mark.parametrize("W", [8, 16, 24])
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("W", [8, 16, 32])
 @pytest.mark.parametrize("P", [1, 2, 4])
-def test_fast_path_plans(gpu, W, P):
-    # queries long enough that most chunks take the fast path; odd and even lengths
-    for N in (1501, 1200):
+def test_fast_path_plans(gpu, W, P, RT):
+    # queries long enough that most chunks take the fast path; lengths of every residue mod 4
+    for N in (1501, 1202, 1403, 1200):
         w = inputs.tiny(B=2, N=N, M=20000, seed=79 + N)
-        cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P)
+        cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
         assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
         wi = inputs.paper_i8(B=2, N=N, M=20000, seed=80 + N)
-        cost, end = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P)
+        cost, end = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT)
         assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
 
 
