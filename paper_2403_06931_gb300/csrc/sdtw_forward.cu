@@ -228,6 +228,7 @@ fwd_chain_kernel(const FwdArgs a)
     // next one R/RT steps later, so rows are staged and written out per group
     // of G = min(32, R/RT) lanes
     const int G = CKPT ? min(32, a.R / RT) : 32;
+    const int logR = CKPT ? __ffs(a.R) - 1 : 0;  // R is a power of two
 
     for (int it = 0;; ++it) {
         int q;
@@ -383,12 +384,15 @@ fwd_chain_kernel(const FwdArgs a)
                         if ((((pg + 1) * RT) & (a.R - 1)) == 0) {
                             __syncwarp();
                             const int col0 = s * S + warp * 32 * W;
-                            for (int e = lane; e < 32 * W; e += 32) {
-                                const int gl = (e / (G * W)) * G + G - 1;  // last lane of e's group
-                                const int pl = p + lane - gl;
-                                const int m = ((pl + 1) * RT) / a.R - 1;
-                                if (col0 + e < M)
-                                    rck[static_cast<int64_t>(m) * a.M + col0 + e] = rstage[e] + rbase[e / W];
+                            for (int g = 0; g < 32 / G; ++g) {
+                                // group g's lanes staged the row of tile pg - g*G
+                                const int m = (((pg - g * G) + 1) * RT >> logR) - 1;
+                                float* dst = rck + static_cast<int64_t>(m) * a.M + col0 + g * G * W;
+                                const float* src = rstage + g * G * W;
+                                const float* sb = rbase + g * G;
+                                const int lim = M - (col0 + g * G * W);
+                                for (int e = lane; e < G * W; e += 32)
+                                    if (e < lim) dst[e] = src[e] + sb[e / W];
                             }
                             __syncwarp();
                         }
@@ -508,14 +512,18 @@ fwd_chain_kernel(const FwdArgs a)
                         for (int g = G - 1; g < 32; g += G) any |= (hits >> g) & 1u;
                         if (any) {
                             __syncwarp();
-                            for (int e = lane; e < 32 * W; e += 32) {
-                                const int gl = (e / (G * W)) * G + G - 1;
+                            for (int g = 0; g < 32 / G; ++g) {
+                                const int gl = g * G + G - 1;  // the group's last lane
                                 const int sl = __shfl_sync(0xffffffffu, s, gl);
                                 const int pl = __shfl_sync(0xffffffffu, p, gl);
-                                const int col0 = sl * S + warp * 32 * W;
-                                const int m = ((pl + 1) * RT) / a.R - 1;
-                                if (((hits >> gl) & 1u) && col0 + e < M)
-                                    rck[static_cast<int64_t>(m) * a.M + col0 + e] = rstage[e] + rbase[e / W];
+                                if (!((hits >> gl) & 1u)) continue;
+                                const int col0 = sl * S + warp * 32 * W + g * G * W;
+                                const int m = ((pl + 1) * RT >> logR) - 1;
+                                float* dst = rck + static_cast<int64_t>(m) * a.M + col0;
+                                const float* src = rstage + g * G * W;
+                                const float* sb = rbase + g * G;
+                                for (int e = lane; e < G * W; e += 32)
+                                    if (col0 + e < M) dst[e] = src[e] + sb[e / W];
                             }
                             __syncwarp();
                         }
