@@ -28,6 +28,9 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--seg-width", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--keep-checkpoints", action="store_true",
+                    help="the forward stores backward checkpoints (implied by --backward)")
     a = ap.parse_args()
 
     kw = {k: v for k, v in (("B", a.B), ("N", a.N), ("M", a.M)) if v is not None}
@@ -44,8 +47,9 @@ def main():
     offs = torch.from_numpy(w.offsets).to(dev) if w.offsets is not None else None
     N = int(w.lengths.max())
     ctx = SdtwContext(dtype=a.dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=N,
-                      max_total_query_len=qs.numel(), grad=a.backward, keep_checkpoints=a.backward,
-                      seg_width=a.seg_width, warps_per_query=a.warps)
+                      max_total_query_len=qs.numel(), grad=a.backward or a.keep_checkpoints,
+                      keep_checkpoints=a.backward or a.keep_checkpoints,
+                      seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows)
     if a.autotune:
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None
