@@ -208,9 +208,12 @@ fwd_chain_kernel(const FwdArgs a)
     // lanes' column values of a chunk, so both leave as contiguous lines
     float* rstage = stage + warp * 32 * W;                         // [P][32][W]
     float* rbase = stage + (CKPT ? P * 32 * W : 0) + warp * 32;     // [P][32]
-    float* cstage_all = stage + (CKPT ? P * 32 * (W + 1) : 0);      // [P][nslot][RT*kChunk]
-    float* cstage = cstage_all + warp * nslot * RT * kChunk;
-    V* xs = reinterpret_cast<V*>(cstage_all + P * nslot * RT * kChunk);  // [Npad]
+    // column staging slots are RT*kChunk + 1 floats apart, so that the
+    // checkpoint lanes' simultaneous stores fall in different banks
+    constexpr int CS = RT * kChunk + 1;
+    float* cstage_all = stage + (CKPT ? P * 32 * (W + 1) : 0);      // [P][nslot][CS]
+    float* cstage = cstage_all + warp * nslot * CS;
+    V* xs = reinterpret_cast<V*>(cstage_all + (P * nslot * CS + 3) / 4 * 4);  // [Npad], 16-byte aligned
     V* red_v = xs + Npad;                                                // [P]
     int* red_i = reinterpret_cast<int*>(red_v + P);                      // [P]
 
@@ -326,7 +329,7 @@ fwd_chain_kernel(const FwdArgs a)
                 float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
                 if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
                 const int p_start = p;
-                float* cslot = (CKPT && ck) ? cstage + (((lane + 1) * W) / a.K - 1) * RT * kChunk : nullptr;
+                float* cslot = (CKPT && ck) ? cstage + (((lane + 1) * W) / a.K - 1) * CS : nullptr;
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
@@ -413,7 +416,7 @@ fwd_chain_kernel(const FwdArgs a)
                             float* d = reinterpret_cast<float*>(__shfl_sync(
                                 0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
                             if (d) {
-                                for (int e = lane; e < RT * kChunk; e += 32) d[e] = cstage[j * RT * kChunk + e];
+                                for (int e = lane; e < RT * kChunk; e += 32) d[e] = cstage[j * CS + e];
                             }
                         }
                         __syncwarp();
@@ -640,12 +643,13 @@ int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K, int RT)
     // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
     // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
     // 4-byte elements; with checkpoints (K > 0) the row staging [P][32][W], its
-    // bases [P][32] and the column staging [P][32W/K][RT*kChunk] floats
+    // bases [P][32] and the column staging [P][32W/K][RT*kChunk + 1] floats
+    // (rounded up to 16 bytes)
     (void)dt;
     const int npad = (N + RT - 1) / RT * RT;
     const int esz = RT == 2 ? 16 : 32;
     int bytes = esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
-    if (K > 0) bytes += 4 * P * (32 * W + 32 + (32 * W / K) * RT * kChunk);
+    if (K > 0) bytes += 4 * P * (32 * W + 32) + 4 * ((P * (32 * W / K) * (RT * kChunk + 1) + 3) / 4 * 4);
     return bytes;
 }
 
