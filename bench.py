@@ -139,7 +139,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     ctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N, grad=True, keep_checkpoints=True)
-    tuned = ctx.autotune(ref, qs)
+    tuned = ctx.plan(B, N, M) if args.no_autotune else ctx.autotune(ref, qs)
     h = ctx.handle
     P = lambda t: t.data_ptr()  # noqa: E731
 
@@ -207,7 +207,8 @@ def run_ours(args, rank, world, local_rank):
             e2e_ctx.handle, P(t_ref), M, P(t_q), None, B, N, P(t_gc), P(t_cost), P(t_end), P(t_gq), P(t_gr), None,
             sp), "sdtw_forward_backward_host", e2e_ctx.handle)
 
-    e2e_ctx.autotune(ref, qs)
+    if not args.no_autotune:
+        e2e_ctx.autotune(ref, qs)
     for _ in range(2):
         e2e_step()
     e2e_ms = []
@@ -297,7 +298,7 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
 
     # forward only, no checkpoints
     fctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N)
-    fplan = fctx.autotune(ref, qs)
+    fplan = fctx.plan(B, N, M) if args.no_autotune else fctx.autotune(ref, qs)
     fctx.forward(ref, qs, out=(cost, end))
     ms = timed(lambda: fctx.forward(ref, qs, out=(cost, end)), 5)
     forms["forward_f32"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": fplan}
@@ -309,7 +310,7 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
     qi = torch.from_numpy(wi.queries).to(dev)
     ci = torch.empty(B, dtype=torch.int32, device=dev)
     ictx = SdtwContext(dtype="i8", max_ref_len=M, max_batch=B, max_query_len=N)
-    iplan = ictx.autotune(ri, qi)
+    iplan = ictx.plan(B, N, M) if args.no_autotune else ictx.autotune(ri, qi)
     ictx.forward(ri, qi, out=(ci, end))
     ms = timed(lambda: ictx.forward(ri, qi, out=(ci, end)), 5)
     forms["forward_i8"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": iplan}
@@ -324,7 +325,7 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
         cr = torch.empty(wr.B, device=dev)
         er = torch.empty(wr.B, dtype=torch.int64, device=dev)
         rctx = SdtwContext(max_ref_len=wr.M, max_batch=wr.B, max_query_len=Nr, max_total_query_len=qr.numel())
-        rplan = rctx.autotune(rr, qr, offsets=orr, N=Nr)
+        rplan = rctx.plan(wr.B, Nr, wr.M, ragged=True) if args.no_autotune else rctx.autotune(rr, qr, offsets=orr, N=Nr)
         rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
@@ -443,6 +444,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the forward/int8/ragged side measurements")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged persistent form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's default plans instead of timing candidates (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

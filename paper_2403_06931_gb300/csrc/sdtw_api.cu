@@ -143,10 +143,12 @@ int64_t nblk_of(int64_t M, int K) { return K > 0 ? M / K : 0; }
 // default plan for a forward call
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
+    // defaults measured on the paper's batch: 24 columns x 4 rows per thread
+    // without checkpoints; 32 x 2 with them (their staging would cost a CTA per SM)
     FwdPlan p;
-    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 32;
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : 24);
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
-    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
+    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : (ckpt ? 2 : 4);
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
         if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
