@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SDTW_ABI_VERSION 2
+#define SDTW_ABI_VERSION 3
 
 typedef struct sdtw_ctx sdtw_ctx;
 
@@ -77,8 +77,8 @@ typedef struct sdtw_config {
     int32_t max_query_len;       /* largest N (the longest query of a ragged batch) */
     int32_t seg_width;           /* reference columns per thread (the paper's segment width); 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
-    int32_t ckpt_stride;         /* columns between backward column checkpoints (64, 128, 256); 0 = chosen under mem_cap_bytes */
-    int32_t ckpt_row_stride;     /* rows between backward row checkpoints (64, 128, 256); 0 = chosen under mem_cap_bytes */
+    int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints; 0 = 32 (the only stride this build has) */
+    int32_t reserved0;           /* must be 0 */
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
     uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
     uint32_t flags;              /* SDTW_FLAG_* */
@@ -94,11 +94,11 @@ typedef struct sdtw_plan {
     int64_t grid;            /* CTAs launched */
     int32_t block;           /* threads per CTA */
     int32_t smem_bytes;      /* dynamic shared memory per CTA */
-    int32_t ckpt_stride;     /* K: columns between checkpoints (0 when none are stored); rows: ckpt_row_stride of the config in use */
+    int32_t ckpt_stride;     /* forward steps between wavefront checkpoints (0 when none are stored) */
     int32_t tuned;           /* 1 if chosen by timing candidates, 0 if the default */
     int64_t sweep_cols;      /* reference columns covered by one sweep of the chain */
     int32_t tile_rows;       /* query rows a thread advances per step */
-    int32_t reserved;
+    int32_t ckpt_cols;       /* K = 8 * seg_width: columns between boundary-column checkpoints (0 when none) */
 } sdtw_plan;
 
 /* ABI version this library was built with (SDTW_ABI_VERSION). */
@@ -154,9 +154,13 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
  * The warp path of each query is recovered by walking back from (N_q-1, end[q])
  * (Section 2's walk-back: to the neighbour (i-1,j-1), (i,j-1) or (i-1,j) of
  * smallest D, exact ties to the first of that list, column 0 upwards, stopping
- * at row 0).  The DP is recomputed tile by tile from the D values the forward
- * stored along every ckpt_stride-th column and every ckpt_row_stride-th row;
- * the full matrix is never stored.
+ * at row 0).  The DP is recomputed band by band from checkpoints of the
+ * forward: its wavefront (an anti-diagonal staircase of rows, one per thread)
+ * every ckpt_stride steps, and the boundary column of every K-column window
+ * (K = 8 * seg_width); each band is recomputed with the forward's own FP32
+ * operations, so the values are the forward's bit for bit.  The full matrix is
+ * never stored.  Under mem_cap_bytes the batch may run in chunks of queries,
+ * each re-running its forward with checkpoint stores.
  * Along the path, d cost/d x_i += 2 (x_i - y_j) and d cost/d y_j += -2 (x_i - y_j).
  *   ref, queries, offsets, B, N, M: as in sdtw_forward (float).
  *   end         device int64 [B]: the end columns sdtw_forward returned.

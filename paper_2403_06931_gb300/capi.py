@@ -30,7 +30,7 @@ SDTW_FLAG_GRAD = 0x1
 SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 
 class sdtw_config(ctypes.Structure):
@@ -44,7 +44,7 @@ class sdtw_config(ctypes.Structure):
         ("seg_width", ctypes.c_int32),
         ("warps_per_query", ctypes.c_int32),
         ("ckpt_stride", ctypes.c_int32),
-        ("ckpt_row_stride", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
         ("mem_cap_bytes", ctypes.c_size_t),
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),
@@ -65,7 +65,7 @@ class sdtw_plan(ctypes.Structure):
         ("tuned", ctypes.c_int32),
         ("sweep_cols", ctypes.c_int64),
         ("tile_rows", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("ckpt_cols", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -49,13 +49,14 @@ int bucket_of(int64_t v)
     return b;
 }
 
+// the inputs and plan of the forward whose checkpoints the workspace holds
 struct CkptKey {
     const void* ref = nullptr;
     const void* queries = nullptr;
     const int64_t* offsets = nullptr;
     int64_t M = 0;
     int32_t B = 0, N = 0;
-    int32_t K = 0;
+    int32_t W = 0, P = 0, RT = 0;
     bool valid = false;
 };
 
@@ -72,17 +73,10 @@ struct sdtw_ctx {
     int* d_queue = nullptr;
     int32_t* d_order = nullptr;
 
-    // backward workspace
-    float* d_ckpt = nullptr;   // column checkpoints
-    size_t ckpt_elems = 0;
-    float* d_rowck = nullptr;  // row checkpoints
-    size_t rowck_elems = 0;
-    int K_min = 0;        // smallest checkpoint stride the workspace holds for a full chunk
-    int K = 0;            // column checkpoint stride in use
-    int R = 0;            // row checkpoint stride in use
-    int bwd_chunk = 0;    // queries per backward chunk
-    float* d_gyq = nullptr;
-    int64_t* d_span = nullptr;
+    // backward workspace: one arena, carved per call into the checkpoint
+    // slots, gradient rows and per-query scalars of a chunk of queries
+    float* d_arena = nullptr;
+    size_t arena_floats = 0;
     void* d_cost_tmp = nullptr;
     int64_t* d_end_tmp = nullptr;
     CkptKey key;
@@ -138,17 +132,15 @@ sdtw_status ensure(sdtw_ctx* c, DevBuf& b, size_t bytes)
     return s;
 }
 
-int64_t nblk_of(int64_t M, int K) { return K > 0 ? M / K : 0; }
-
 // default plan for a forward call
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
-    // defaults measured on the paper's batch: 24 columns x 4 rows per thread
-    // without checkpoints; 32 x 2 with them (their staging would cost a CTA per SM)
+    // defaults measured on the paper's batch: 24 columns x 4 rows per thread,
+    // four warps per query
     FwdPlan p;
-    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : 24);
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 24;
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
-    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : (ckpt ? 2 : 4);
+    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
         if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
@@ -158,9 +150,8 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
     // a short reference needs fewer threads per query (unless the caller fixed P)
     if (c->cfg.warps_per_query <= 0)
         while (p.P > 1 && static_cast<int64_t>(32) * (p.P / 2) * p.W >= M) p.P /= 2;
-    if (ckpt && c->K % p.W != 0) p.W = 16;
     p.block = 32 * p.P;
-    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, ckpt ? c->K : 0, p.RT);
+    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, p.RT);
     p.persistent = ragged;
     if (p.persistent) {
         int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
@@ -183,12 +174,68 @@ sdtw_status check_common(sdtw_ctx* c, const void* ref, int64_t M, const void* qu
     return SDTW_OK;
 }
 
+// Backward workspace of a checkpointing plan, per query of a chunk (floats):
+// the wavefront slot, the boundary columns, the reference-gradient row and
+// the scalars (cost, end, span).
+struct CkLayout {
+    int64_t fr_slot = 0, ck_slot = 0, per_q = 0;
+    int K = 0;
+};
+
+CkLayout ck_layout(int64_t M, int N, const FwdPlan& p)
+{
+    CkLayout l;
+    l.K = 8 * p.W;
+    l.fr_slot = sdtw::fr_slot_floats(M, N, p.W, p.P, p.RT);
+    l.ck_slot = sdtw::ck_slot_floats(M, N, l.K);
+    l.per_q = l.fr_slot + l.ck_slot + M + 7;
+    return l;
+}
+
+constexpr int64_t kCarveSlack = 32;  // rounding of the carved arrays to 16 bytes
+
+// queries whose checkpoints fit in the arena at once
+int64_t chunk_capacity(const sdtw_ctx* c, const CkLayout& l)
+{
+    if (c->arena_floats <= static_cast<size_t>(kCarveSlack)) return 0;
+    return static_cast<int64_t>((c->arena_floats - kCarveSlack) / static_cast<size_t>(l.per_q));
+}
+
+// checkpoint arrays of a chunk of nq queries, carved from the arena
+struct CkPtrs {
+    float* fr = nullptr;
+    int64_t fr_slot = 0;
+    float* colck = nullptr;
+    int64_t ck_slot = 0;
+    int K = 0;
+    float* gyq = nullptr;
+    float* ck_cost = nullptr;
+    int64_t* ck_end = nullptr;
+    int64_t* span = nullptr;
+};
+
+CkPtrs carve(const sdtw_ctx* c, const CkLayout& l, int64_t nq, int64_t M)
+{
+    auto r4 = [](int64_t v) { return (v + 3) / 4 * 4; };
+    CkPtrs k;
+    k.fr_slot = l.fr_slot;
+    k.ck_slot = l.ck_slot;
+    k.K = l.K;
+    k.fr = c->d_arena;
+    k.colck = k.fr + nq * l.fr_slot;
+    k.gyq = k.colck + r4(nq * l.ck_slot);
+    k.ck_cost = k.gyq + r4(nq * M);
+    k.ck_end = reinterpret_cast<int64_t*>(k.ck_cost + r4(nq));
+    k.span = k.ck_end + r4(nq);
+    return k;
+}
+
 sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
                         int32_t B, int32_t N, void* cost, int64_t* end, cudaStream_t s, const FwdPlan* force,
-                        float* ckpt, int32_t q0, int32_t nq)
+                        const CkPtrs* ck, int32_t q0, int32_t nq)
 {
     const bool ragged = offsets != nullptr;
-    FwdPlan p = force ? *force : default_fwd_plan(c, nq, N, M, ragged, ckpt != nullptr);
+    FwdPlan p = force ? *force : default_fwd_plan(c, nq, N, M, ragged, ck != nullptr);
     if (p.smem > kMaxSmem) return SDTW_E_UNSUPPORTED;
     if (sdtw::fwd_total_steps(M, N, p.W, p.P, p.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (p.persistent) p.grid = std::min(p.grid, nq);
@@ -204,12 +251,17 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     a.B_total = B;
     a.cost = cost;
     a.end = end;
-    a.ckpt = ckpt;
-    a.rowck = ckpt ? c->d_rowck : nullptr;
-    a.K = ckpt ? c->K : 1;
-    a.R = ckpt ? c->R : 2;
-    a.nblk = ckpt ? nblk_of(M, c->K) : 0;
-    a.ckpt_rows = ckpt ? static_cast<int64_t>(c->bwd_chunk) * c->cfg.max_query_len : 0;
+    if (ck) {
+        a.fr = ck->fr;
+        a.fr_slot = ck->fr_slot;
+        a.colck = ck->colck;
+        a.ck_slot = ck->ck_slot;
+        a.K = ck->K;
+        a.ck_cost = ck->ck_cost;
+        a.ck_end = ck->ck_end;
+    } else {
+        a.K = 1;
+    }
     a.status = c->d_status;
     a.queue = nullptr;
     a.order = nullptr;
@@ -230,54 +282,19 @@ sdtw_status alloc_backward(sdtw_ctx* c)
 {
     const sdtw_config& f = c->cfg;
     const int64_t M = f.max_ref_len;
-    const int64_t N = f.max_query_len;
-    // (column stride K, row stride R) candidates, most preferred first: tiles
-    // wider than tall suit paths that stretch along the reference
-    int cand[6][2] = {{256, 64}, {256, 128}, {256, 256}, {128, 256}, {64, 256}, {0, 0}};
-    int ncand = 5;
-    if (f.ckpt_stride > 0 || f.ckpt_row_stride > 0) {
-        const int K = f.ckpt_stride > 0 ? f.ckpt_stride : 256;
-        const int R = f.ckpt_row_stride > 0 ? f.ckpt_row_stride : 64;
-        if (!sdtw::bwd_stride_supported(K) || !sdtw::bwd_row_stride_supported(R)) return SDTW_E_INVALID;
-        cand[0][0] = K;
-        cand[0][1] = R;
-        ncand = 1;
-    }
-    // cost/end scratch for the forward re-run is sized by max_batch, not by the chunk
+    const int N = f.max_query_len;
+    // one arena for the default checkpointing plan at the configured maxima:
+    // the whole batch if the cap allows, else as many queries as fit (the
+    // backward then runs in chunks of queries)
+    const FwdPlan p = default_fwd_plan(c, f.max_batch, N, M, false, true);
+    const CkLayout l = ck_layout(M, N, p);
     const size_t fixed = c->ws_bytes + 12 * static_cast<size_t>(f.max_batch);
-    int best = -1;
-    int64_t best_fit = 0;
-    for (int i = 0; i < ncand; ++i) {
-        // per query: column and row checkpoints, gradient row M floats, span
-        const size_t per_q = 4 * sdtw::ckpt_floats_per_query(N, M, cand[i][0], cand[i][1]) +
-                             4 * static_cast<size_t>(M) + 32;
-        if (fixed + per_q > c->cap) continue;
-        const int64_t fit = static_cast<int64_t>((c->cap - fixed) / per_q);
-        if (fit > best_fit) {
-            best = i;
-            best_fit = fit;
-        }
-        if (fit >= f.max_batch) {
-            best = i;
-            break;
-        }
-    }
-    if (best < 0) return SDTW_E_NOMEM;
-    const int K = cand[best][0], R = cand[best][1];
-    const int chunk = static_cast<int>(std::min<int64_t>(best_fit >= f.max_batch ? f.max_batch : best_fit, f.max_batch));
-    c->K = K;
-    c->R = R;
-    c->K_min = K;
-    c->bwd_chunk = chunk;
-    c->ckpt_elems = static_cast<size_t>(N) * nblk_of(M, K) * chunk;
-    c->rowck_elems = static_cast<size_t>(static_cast<int64_t>(chunk) * N / R) * static_cast<size_t>(M);
+    if (fixed + 4 * static_cast<size_t>(l.per_q + kCarveSlack) > c->cap) return SDTW_E_NOMEM;
+    const size_t want = static_cast<size_t>(l.per_q) * f.max_batch + kCarveSlack;
+    const size_t fit = (c->cap - fixed) / 4;
+    c->arena_floats = std::min(want, fit);
     sdtw_status s;
-    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_ckpt), 4 * std::max<size_t>(c->ckpt_elems, 1))) != SDTW_OK)
-        return s;
-    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_rowck), 4 * std::max<size_t>(c->rowck_elems, 1))) != SDTW_OK)
-        return s;
-    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_gyq), 4 * static_cast<size_t>(M) * chunk)) != SDTW_OK) return s;
-    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_span), 16 * static_cast<size_t>(chunk))) != SDTW_OK) return s;
+    if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_arena), 4 * c->arena_floats)) != SDTW_OK) return s;
     if ((s = dev_alloc(c, &c->d_cost_tmp, 4 * static_cast<size_t>(f.max_batch))) != SDTW_OK) return s;
     if ((s = dev_alloc(c, reinterpret_cast<void**>(&c->d_end_tmp), 8 * static_cast<size_t>(f.max_batch))) != SDTW_OK)
         return s;
@@ -289,10 +306,7 @@ void free_all(sdtw_ctx* c)
     dev_free(c, c->d_status, sizeof(int));
     dev_free(c, c->d_queue, sizeof(int));
     dev_free(c, c->d_order, 4 * static_cast<size_t>(c->cfg.max_batch));
-    dev_free(c, c->d_ckpt, 4 * std::max<size_t>(c->ckpt_elems, 1));
-    dev_free(c, c->d_rowck, 4 * std::max<size_t>(c->rowck_elems, 1));
-    dev_free(c, c->d_gyq, 4 * static_cast<size_t>(c->cfg.max_ref_len) * c->bwd_chunk);
-    dev_free(c, c->d_span, 16 * static_cast<size_t>(c->bwd_chunk));
+    dev_free(c, c->d_arena, 4 * c->arena_floats);
     dev_free(c, c->d_cost_tmp, 4 * static_cast<size_t>(c->cfg.max_batch));
     dev_free(c, c->d_end_tmp, 8 * static_cast<size_t>(c->cfg.max_batch));
     for (DevBuf* b : {&c->st_ref, &c->st_q, &c->st_off, &c->st_cost, &c->st_end, &c->st_gc, &c->st_gq, &c->st_gr,
@@ -301,10 +315,21 @@ void free_all(sdtw_ctx* c)
 }
 
 bool key_matches(const CkptKey& k, const void* ref, int64_t M, const void* q, const int64_t* off, int32_t B,
-                 int32_t N, int K)
+                 int32_t N)
 {
-    return k.valid && k.ref == ref && k.M == M && k.queries == q && k.offsets == off && k.B == B && k.N == N &&
-           k.K == K;
+    return k.valid && k.ref == ref && k.M == M && k.queries == q && k.offsets == off && k.B == B && k.N == N;
+}
+
+// the plan a checkpointing forward of this shape runs, and whether the whole
+// batch's checkpoints fit in the arena
+FwdPlan ckpt_plan(const sdtw_ctx* c, int32_t B, int32_t N, int64_t M, bool ragged)
+{
+    return default_fwd_plan(c, B, N, M, ragged, true);
+}
+
+bool keep_fits(const sdtw_ctx* c, int32_t B, int32_t N, int64_t M, const FwdPlan& p)
+{
+    return (c->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= chunk_capacity(c, ck_layout(M, N, p));
 }
 
 }  // namespace
@@ -351,6 +376,8 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
+    if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0) return SDTW_E_INVALID;
+    if (cfg->ckpt_stride != 0 && cfg->ckpt_stride != sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
     if (cfg->dtype == SDTW_I8 && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
 
@@ -400,22 +427,27 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
     if (B == 0) return SDTW_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    float* ckpt = nullptr;
-    const bool keep = (ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk;
-    if (keep) ckpt = ctx->d_ckpt;
     ctx->key.valid = false;
-    s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, ckpt, 0, B);
-    if (s == SDTW_OK && keep) {
-        ctx->key.ref = ref;
-        ctx->key.queries = queries;
-        ctx->key.offsets = offsets;
-        ctx->key.M = M;
-        ctx->key.B = B;
-        ctx->key.N = N;
-        ctx->key.K = ctx->K * 1000 + ctx->R;
-        ctx->key.valid = true;
+    const FwdPlan cp = ckpt_plan(ctx, B, N, M, offsets != nullptr);
+    if (keep_fits(ctx, B, N, M, cp)) {
+        // store the checkpoints a following sdtw_backward on these inputs reuses
+        const CkPtrs ck = carve(ctx, ck_layout(M, N, cp), B, M);
+        s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &cp, &ck, 0, B);
+        if (s == SDTW_OK) {
+            ctx->key.ref = ref;
+            ctx->key.queries = queries;
+            ctx->key.offsets = offsets;
+            ctx->key.M = M;
+            ctx->key.B = B;
+            ctx->key.N = N;
+            ctx->key.W = cp.W;
+            ctx->key.P = cp.P;
+            ctx->key.RT = cp.RT;
+            ctx->key.valid = true;
+        }
+        return s;
     }
-    return s;
+    return run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, nullptr, 0, B);
 }
 
 sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
@@ -429,7 +461,6 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
     if (s != SDTW_OK) return s;
     if (B > 0 && (!grad_queries || !grad_ref)) return SDTW_E_INVALID;
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
-    if (sdtw::bwd_smem_bytes(N, ctx->K, ctx->R) > kMaxSmem) return SDTW_E_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (B == 0) {
@@ -437,13 +468,25 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         if ((e = cudaMemsetAsync(grad_ref, 0, 4 * static_cast<size_t>(M), st)) != cudaSuccess) return cuda_fail(ctx, e);
         return SDTW_OK;
     }
-    const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N, ctx->K * 1000 + ctx->R);
-    const int chunk = ctx->bwd_chunk;
+    // the plan of the checkpoints: the kept forward's, or the one re-run here
+    const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N);
+    FwdPlan p = ckpt_plan(ctx, B, N, M, offsets != nullptr);
+    if (reuse) {
+        p.W = ctx->key.W;
+        p.P = ctx->key.P;
+        p.RT = ctx->key.RT;
+    }
+    if (!sdtw::bwd_width_supported(p.W)) return SDTW_E_UNSUPPORTED;
+    if (sdtw::bwd_smem_bytes(N, p.W, p.RT) > kMaxSmem) return SDTW_E_UNSUPPORTED;
+    const CkLayout l = ck_layout(M, N, p);
+    const int64_t cap = chunk_capacity(ctx, l);
+    if (cap < 1) return SDTW_E_NOMEM;
+    const int chunk = reuse ? B : static_cast<int>(std::min<int64_t>(B, cap));
+    const CkPtrs ck = carve(ctx, l, chunk, M);
     for (int q0 = 0; q0 < B; q0 += chunk) {
         const int nq = std::min(chunk, B - q0);
         if (!reuse) {
-            s = run_forward(ctx, ref, M, queries, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, nullptr,
-                            ctx->d_ckpt, q0, nq);
+            s = run_forward(ctx, ref, M, queries, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, &p, &ck, q0, nq);
             if (s != SDTW_OK) return s;
         }
         sdtw::BwdArgs a{};
@@ -459,17 +502,21 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         a.grad_cost = grad_cost;
         a.grad_queries = grad_queries;
         a.path = path;
-        a.ckpt = ctx->d_ckpt;
-        a.rowck = ctx->d_rowck;
-        a.K = ctx->K;
-        a.R = ctx->R;
-        a.nblk = nblk_of(M, ctx->K);
-        a.ckpt_rows = static_cast<int64_t>(ctx->bwd_chunk) * ctx->cfg.max_query_len;
-        a.gyq = ctx->d_gyq;
-        a.span = ctx->d_span;
+        a.fr = ck.fr;
+        a.fr_slot = ck.fr_slot;
+        a.colck = ck.colck;
+        a.ck_slot = ck.ck_slot;
+        a.K = ck.K;
+        a.ck_cost = ck.ck_cost;
+        a.ck_end = ck.ck_end;
+        a.W = p.W;
+        a.P = p.P;
+        a.RT = p.RT;
+        a.gyq = ck.gyq;
+        a.span = ck.span;
         a.status = ctx->d_status;
         if ((e = sdtw::launch_backward_walk(a, st)) != cudaSuccess) return cuda_fail(ctx, e);
-        if ((e = sdtw::launch_grad_ref_reduce(ctx->d_gyq, ctx->d_span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
+        if ((e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
             return cuda_fail(ctx, e);
     }
     if (!reuse) ctx->key.valid = false;
@@ -580,7 +627,9 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     if (B == 0) return SDTW_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool ragged = offsets != nullptr;
-    const bool ckpt = (ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk;
+    // with kept checkpoints, time the checkpointing forward (its stores
+    // included) among the plans whose checkpoints fit the arena
+    const bool ckpt = keep_fits(ctx, B, N, M, ckpt_plan(ctx, B, N, M, ragged));
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
     float best_ms = 1e30f;
@@ -590,7 +639,6 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     const int RTs[] = {2, 4};
     for (int RT : RTs) {
         for (int W : Ws) {
-            if (ckpt && ctx->K % W != 0) continue;
             for (int P : Ps) {
                 if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
                 FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
@@ -598,8 +646,11 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 p.P = P;
                 p.RT = RT;
                 p.block = 32 * P;
-                p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, ckpt ? ctx->K : 0, RT);
+                p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, RT);
                 if (p.smem > kMaxSmem) continue;
+                const CkLayout l = ck_layout(M, N, p);
+                if (ckpt && B > chunk_capacity(ctx, l)) continue;
+                const CkPtrs ck = ckpt ? carve(ctx, l, B, M) : CkPtrs{};
                 const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
                 if (per_sm <= 0) continue;
                 p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : B;
@@ -607,8 +658,8 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
                     cudaEventRecord(e0, st);
-                    s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p,
-                                    ckpt ? ctx->d_ckpt : nullptr, 0, B);
+                    s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, ckpt ? &ck : nullptr,
+                                    0, B);
                     cudaEventRecord(e1, st);
                     if (s != SDTW_OK) break;
                     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -651,9 +702,9 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
                           sdtw_plan* plan)
 {
     if (!ctx || !plan || B < 1 || N < 1 || M < 1) return SDTW_E_INVALID;
-    const bool ckpt = backward || ((ctx->cfg.flags & SDTW_FLAG_KEEP_CHECKPOINTS) && B <= ctx->bwd_chunk);
     if (backward && !(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
-    FwdPlan p = default_fwd_plan(ctx, backward ? std::min(B, ctx->bwd_chunk) : B, N, M, ragged != 0, ckpt);
+    const bool ckpt = backward || keep_fits(ctx, B, N, M, ckpt_plan(ctx, B, N, M, ragged != 0));
+    FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged != 0, ckpt);
     std::memset(plan, 0, sizeof(*plan));
     plan->seg_width = p.W;
     plan->warps_per_query = p.P;
@@ -662,7 +713,8 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
     plan->grid = p.persistent ? p.grid : B;
     plan->block = p.block;
     plan->smem_bytes = p.smem;
-    plan->ckpt_stride = ckpt ? ctx->K : 0;
+    plan->ckpt_stride = ckpt ? sdtw::kChunk : 0;
+    plan->ckpt_cols = ckpt ? 8 * p.W : 0;
     plan->tuned = ctx->tuned.count(TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0})
                       ? 1
                       : 0;

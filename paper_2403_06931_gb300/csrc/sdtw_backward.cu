@@ -7,24 +7,27 @@
 //   d cost / d x_i = sum over the path's cells in row i    of  2 (x_i - y_j)
 //   d cost / d y_j = sum over the path's cells in column j of -2 (x_i - y_j).
 //
-// The n x M matrix is never stored.  The forward pass left absolute D values
-// along every K-th column and every R-th row (its checkpoints), so the matrix
-// splits into R x K tiles whose top row and left column are known.  The walk
-// proceeds tile by tile, one warp per query:
-//   * the warp recomputes the tile's rows down to the current cell from the
-//     checkpoint row above and the checkpoint column on the left (FP32
-//     relative to per-lane integer bases, rebased every kChunk rows as in the
-//     forward), with the same three-input minimum as the forward on the
-//     dependency chain; each cell's walk-back choice (two bits) is derived
-//     off the chain by equality with that minimum (diagonal first, then left,
-//     then up -- the tie order of the walk-back);
+// The n x M matrix is never stored.  The checkpointing forward left, at the
+// start of every chunk of kChunk steps, its wavefront (each thread's latest
+// row, the right-hand cells of its tile's other rows, its diagonal input and
+// its integer base: an anti-diagonal staircase of rows), and the left inputs
+// of every strip that starts a K-column window (K = 8 W).  The cells that the
+// eight strips of one window computed during one chunk form a band, a
+// parallelogram (each strip one tile higher than its left neighbour).  The
+// walk proceeds band by band, one warp per query:
+//   * the warp recomputes the band's rows down to the current cell from the
+//     chunk's wavefront and the window's boundary column, with the forward's
+//     own operations in the forward's own bases (four lanes per strip, W/4
+//     columns each, lane l one row behind lane l-1), so every value is the
+//     forward's bit for bit; each cell's walk-back choice (two bits) is read
+//     off the minimum by equality (diagonal first, then left, then up -- the
+//     tie order of the walk-back);
 //   * the walk itself is cooperative: the 32 lanes read 32 cells of the
 //     current row at once and a ballot finds where the path leaves the row,
 //     so a horizontal run of the path costs one step per 32 cells; the row's
 //     gradient is a warp sum and finished columns are written in parallel.
-// Paths that stretch far along the reference (a query rescaled by its own
-// z-normalisation typically moves several columns per row) cross many tiles,
-// so tiles are wider (K = 256) than tall (R = 64 by default).
+// At the first band the recomputed end cell must equal the forward's cost
+// exactly; a mismatch sets a status bit.
 //
 // Per-query reference gradients go to rows of a scratch buffer, only over the
 // path's column span; a second kernel sums them over queries in query order,
@@ -46,6 +49,8 @@ struct DirWord<2> { using T = uint8_t; };
 template <>
 struct DirWord<4> { using T = uint8_t; };
 template <>
+struct DirWord<6> { using T = uint16_t; };
+template <>
 struct DirWord<8> { using T = uint16_t; };
 
 constexpr int kDiag = 0, kLeft = 1, kUp = 2, kOutside = 3;
@@ -58,11 +63,14 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 template <int WB>
-__global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
+__global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
 {
     using DW = typename DirWord<WB>::T;
-    constexpr int KC = 32 * WB;  // tile columns
-    const int R = a.R;           // tile rows
+    constexpr int W = 4 * WB;    // forward segment width: four lanes per strip
+    constexpr int KW = 32 * WB;  // window width K = 8 W
+    const int RT = a.RT;
+    const int L = 32 * a.P;
+    const int S = L * W;
     const int lane = threadIdx.x;
     const int N = a.N;
     const int M = static_cast<int>(a.M);
@@ -71,21 +79,18 @@ __global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
     const float INF = __int_as_float(0x7f800000);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* xs = reinterpret_cast<float*>(smem_raw);  // [N]  query samples
-    float* ys = xs + N;                              // [KC] reference samples of the tile
-    float* top = ys + KC;                            // [KC] D of the row above the tile (absolute)
-    float* lcol = top + KC;                          // [R]  D of the column left of the tile (absolute)
-    DW* dirs = reinterpret_cast<DW*>(lcol + R);      // [R][32] walk-back choices, 2 bits per cell
+    float* xs = reinterpret_cast<float*>(smem_raw);  // [N] query samples
+    float* ys = xs + N;                              // [KW] reference samples of the window
+    float* lcol = ys + KW;                           // [RT*kChunk] the window's boundary column
+    DW* dirs = reinterpret_cast<DW*>(lcol + RT * kChunk);  // [steps][32] walk-back choices
 
-    const int64_t first_start = a.offsets ? a.offsets[a.q0] : static_cast<int64_t>(a.q0) * N;
     int64_t start;
     int n;
     if (a.offsets) {
         start = a.offsets[q];
         const int64_t stop = a.offsets[q + 1];
         const int64_t len = stop - start;
-        if (start < first_start || len < 0 || len > N || stop > a.offsets[a.B_total] ||
-            (stop - first_start) > a.ckpt_rows) {
+        if (start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total]) {
             if (lane == 0) {
                 atomicOr(a.status, kStatusBadLength);
                 a.span[2 * ql] = 0;
@@ -117,97 +122,162 @@ __global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
     const float g2 = 2.f * a.grad_cost[q];
     const float* x = a.queries + start;
     for (int i = lane; i < n; i += 32) xs[i] = x[i];
-    const float* cck = a.ckpt + (start - first_start) * a.nblk;      // [nblk][n]
-    const float* rck = a.rowck + ((start - first_start) / R) * a.M;  // [n/R][M]
     float* gyq = a.gyq + static_cast<int64_t>(ql) * a.M;
     float* gq = a.grad_queries + start;
     int32_t* path = a.path ? a.path + 2 * start : nullptr;
+
+    // the forward's schedule for this query (sdtw_forward.cu)
+    const int lag_last = (a.P - 1) * (32 + kChunk) + 31;
+    const int nt = (n + RT - 1) / RT;
+    const int Pp = max(nt, lag_last + kChunk);
+    const int erec = fwd_record_floats(RT);
+    const float* frq = a.fr + static_cast<int64_t>(ql) * a.fr_slot;
+    const float* ckq = a.colck + static_cast<int64_t>(ql) * a.ck_slot;
 
     // walk state, identical in every lane: current cell (wi, wj), the
     // gradient of row wi and of column wj accumulated so far
     int wi = n - 1, wj = static_cast<int>(e64);
     float ax = 0.f, ay = 0.f;
-    bool done = false;
+    bool done = false, first = true;
     if (lane == 0 && path) path[2 * wi + 1] = wj;
 
-    while (!done) {
-        const int rb = wi / R, cb = wj / KC;
-        const int r0 = rb * R, c0 = cb * KC;
-        const int rows = wi - r0 + 1;  // recompute rows r0..wi of the tile
+    const int d = lane >> 2;    // this lane's strip in the window
+    const int sub = lane & 3;   // and its quarter of the strip
 
-        __syncwarp();
-        for (int k = lane; k < KC; k += 32) {
-            const int col = c0 + k;
-            ys[k] = col < M ? a.ref[col] : 0.f;
-            top[k] = (rb > 0 && col < M) ? rck[static_cast<int64_t>(rb - 1) * a.M + col] : 0.f;
-        }
-        for (int k = lane; k < rows; k += 32)
-            lcol[k] = cb > 0 ? cck[static_cast<int64_t>(cb - 1) * n + r0 + k] : INF;
-        // D(r0-1, c0-1): the virtual row -1 is zero, the virtual column -1 infinite
-        const float corner = rb == 0 ? 0.f : (cb > 0 ? rck[static_cast<int64_t>(rb - 1) * a.M + c0 - 1] : INF);
-        __syncwarp();
-
-        // ---- recompute rows r0..wi of the tile, recording walk-back choices
-        {
-            float y[WB], D[WB];
-            float B = floorf(top[lane * WB]);  // per-lane base: absolute D = B + D'
-#pragma unroll
-            for (int k = 0; k < WB; ++k) {
-                y[k] = ys[lane * WB + k];
-                D[k] = top[lane * WB + k] - B;
+    // every band holds at least the walk's current cell, so a path of at most
+    // n + M cells needs at most that many bands
+    for (int64_t guard = 0; !done; ++guard) {
+        // ---- the band holding (wi, wj): window b, chunk c
+        const int b = wj / KW, c0 = b * KW, s = c0 / S;
+        const int tau0 = (c0 - s * S) / W;   // forward thread of the window's first strip
+        const int lag0 = (tau0 >> 5) * (32 + kChunk) + (tau0 & 31);  // strips of a window share a warp
+        const int dj = (wj - c0) / W;
+        const int c = (wi / RT + lag0 + dj + s * Pp) / kChunk;
+        const int ps0 = c * kChunk - lag0 - s * Pp;  // strip 0's tile at the chunk start
+        const int rtop = RT * (ps0 - 7);             // lane l handles row r at step r - rtop + l
+        const int ps = ps0 - d;                      // this lane's strip
+        const int rf = RT * max(0, ps);              // its rows in the band: [rf, re)
+        const int re = min(n, RT * min(nt, ps + kChunk));
+        const int rf_left = RT * max(0, ps + 1);     // the strip on the left starts here
+        const int rf0 = RT * max(0, ps0);
+        const int re0 = min(min(n, RT * min(nt, ps0 + kChunk)), wi + 1);
+        if (guard > static_cast<int64_t>(n) + M || wi < RT * max(0, ps0 - dj) ||
+            wi >= min(n, RT * min(nt, ps0 - dj + kChunk))) {
+            // the current cell is not in its band: report and give up on this query
+            if (lane == 0) {
+                atomicOr(a.status, kStatusReplay);
+                a.span[2 * ql] = 0;
+                a.span[2 * ql + 1] = -1;
             }
-            float diag = (lane == 0 ? corner : top[lane * WB - 1]) - B;
-            const int steps = rows + 31;
-            for (int t = 0; t < steps; ++t) {
-                if (t > 0 && (t & (kChunk - 1)) == 0) {
-                    const float bn = floorf(B + D[0]);
-                    const float dl = bn - B;
+            return;
+        }
+
+        __syncwarp();
+        for (int k = lane; k < KW; k += 32) ys[k] = c0 + k < M ? a.ref[c0 + k] : 0.f;
+        if (b > 0)
+            for (int k = lane; k < re0 - rf0; k += 32) lcol[k] = ckq[static_cast<int64_t>(b - 1) * N + rf0 + k];
+
+        // ---- the lane's starting state: the chunk's wavefront, or the virtual
+        // zero row -1 for a strip that starts its sweep inside the chunk
+        const float* frc = frq + static_cast<int64_t>(c) * L * (W + erec);
+        const int tau = tau0 + d;
+        auto fr_at = [&](int j, int th) { return frc[((j >> 2) * L + th) * 4 + (j & 3)]; };
+        auto rec_at = [&](int e, int th) { return frc[(((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]; };
+        float D[WB], y[WB];
+        float Bl = 0.f, dg = 0.f;
+        if (ps >= 1 && ps <= nt) {
 #pragma unroll
-                    for (int k = 0; k < WB; ++k) D[k] -= dl;
-                    diag -= dl;
-                    B = bn;
-                }
-                float recv = __shfl_up_sync(0xffffffffu, D[WB - 1], 1);
-                float rbs = __shfl_up_sync(0xffffffffu, B, 1);
-                const int r = t - lane;
-                const bool act = static_cast<unsigned>(r) < static_cast<unsigned>(rows);
-                if (lane == 0) {
-                    recv = act ? lcol[r] : INF;  // absolute values
-                    rbs = 0.f;
-                }
-                if (act) {
-                    const float xv = xs[r0 + r];
-                    float left = recv + (rbs - B);
-                    const float conv = left;
-                    uint32_t code = 0;
+            for (int k = 0; k < WB; ++k) D[k] = fr_at(sub * WB + k, tau);
+            Bl = rec_at(RT == 2 ? 2 : 4, tau);
+            dg = sub == 0 ? rec_at(RT - 1, tau) : fr_at(sub * WB - 1, tau);
+        } else {
 #pragma unroll
-                    for (int k = 0; k < WB; ++k) {
-                        const float up = D[k];
-                        const float v = min3_f32(up, diag, left);
-                        const uint32_t c = v == diag ? kDiag : (v == left ? kLeft : kUp);
-                        const float d = xv - y[k];
-                        const float nv = fmaf(d, d, v);
-                        code |= c << (2 * k);
-                        diag = up;
-                        left = nv;
-                        D[k] = nv;
+            for (int k = 0; k < WB; ++k) D[k] = 0.f;
+        }
+        // the first lane of strips 1..7: the left strip's last tile before the
+        // band (rows RT*ps .. RT*ps + RT-1, its right-hand cells) and its base
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, dd = 0.f;
+        if (sub == 0 && d >= 1) {
+            float Bsrc = 0.f;
+            if (ps + 1 >= 1 && ps + 1 <= nt) {
+                e0 = rec_at(0, tau - 1);
+                if (RT == 2) {
+                    e1 = fr_at(W - 1, tau - 1);
+                } else {
+                    e1 = rec_at(1, tau - 1);
+                    e2 = rec_at(2, tau - 1);
+                    e3 = fr_at(W - 1, tau - 1);
+                }
+                Bsrc = rec_at(RT == 2 ? 2 : 4, tau - 1);
+            }
+            dd = Bsrc - Bl;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < WB; ++k) y[k] = ys[lane * WB + k];
+
+        // ---- recompute the band's rows down to row wi, recording choices
+        const int steps = wi - rtop + 32;
+        for (int sg = 0; sg < steps; ++sg) {
+            const float recv = __shfl_up_sync(0xffffffffu, D[WB - 1], 1);
+            const int r = sg + rtop - lane;
+            if (r >= rf && r < re && r <= wi) {
+                float left;
+                if (sub != 0) {
+                    left = recv;  // same strip, same base
+                } else if (d == 0) {
+                    left = b == 0 ? INF : lcol[r - rf0];  // already in this strip's base
+                } else {
+                    float v = recv;
+                    if (r < rf_left) {
+                        const int e = r - RT * ps;
+                        v = e == 0 ? e0 : e == 1 ? e1 : e == 2 ? e2 : e3;
                     }
-                    diag = conv;
-                    dirs[r * 32 + lane] = static_cast<DW>(code);
+                    left = v + dd;  // into this strip's base, as the forward converts
                 }
+                const float xv = xs[r];
+                const float conv = left;
+                uint32_t code = 0;
+#pragma unroll
+                for (int k = 0; k < WB; ++k) {
+                    const float up = D[k];
+                    const float v = min3_f32(up, dg, left);
+                    const uint32_t cc = v == dg ? kDiag : (v == left ? kLeft : kUp);
+                    const float dlt = xv - y[k];
+                    const float nv = fmaf(dlt, dlt, v);
+                    code |= cc << (2 * k);
+                    dg = up;
+                    left = nv;
+                    D[k] = nv;
+                }
+                dg = conv;
+                dirs[sg * 32 + lane] = static_cast<DW>(code);
             }
+        }
+
+        if (first) {
+            // the recomputed end cell against the forward's cost (when the
+            // walk starts at the forward's own end)
+            const int lj = (wj - c0) / WB, kj = (wj - c0) - lj * WB;
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < WB; ++k)
+                if (k == kj) v = D[k];
+            v = __shfl_sync(0xffffffffu, v + Bl, lj);
+            if (lane == 0 && a.ck_end[ql] == e64 && v != a.ck_cost[ql]) atomicOr(a.status, kStatusReplay);
+            first = false;
         }
         __syncwarp();
 
-        // ---- follow the path through the tile, 32 cells of a row at a time
+        // ---- follow the path through the band, 32 cells of a row at a time
         for (;;) {
             const float xi = xs[wi];
             if (wi == 0) {
                 // the path starts here: only this cell of row 0 is on it
-                const float c = g2 * (xi - ys[wj - c0]);
+                const float cg = g2 * (xi - ys[wj - c0]);
                 if (lane == 0) {
-                    gq[0] = ax + c;
-                    gyq[wj] = ay - c;
+                    gq[0] = ax + cg;
+                    gyq[wj] = ay - cg;
                     if (path) path[0] = wj;
                     a.span[2 * ql] = wj;
                     a.span[2 * ql + 1] = e64;
@@ -218,11 +288,9 @@ __global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
             const int jk = wj - lane;
             int code = kOutside;
             if (jk >= c0) {
-                if (jk == 0) {
-                    code = kUp;
-                } else {
-                    const int cc = jk - c0;
-                    code = (dirs[(wi - r0) * 32 + cc / WB] >> (2 * (cc % WB))) & 3;
+                const int cc = jk - c0, lam = cc / WB;
+                if (wi >= RT * max(0, ps0 - (lam >> 2))) {  // row wi is in the band in that strip
+                    code = jk == 0 ? kUp : (dirs[(wi - rtop + lam) * 32 + lam] >> (2 * (cc - lam * WB))) & 3;
                 }
             }
             const unsigned stop = __ballot_sync(0xffffffffu, code != kLeft);
@@ -230,10 +298,10 @@ __global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
             const int fcode = f < 32 ? __shfl_sync(0xffffffffu, code, f) : kLeft;
             const int last = fcode == kOutside ? f - 1 : (f < 32 ? f : 31);  // last lane on the path
             const bool on = lane <= last;
-            const float c = on ? g2 * (xi - ys[jk - c0]) : 0.f;
-            ax += warp_sum(c);
+            const float cg = on ? g2 * (xi - ys[jk - c0]) : 0.f;
+            ax += warp_sum(cg);
             // column of lane k: finished unless the path goes up from it
-            float vy = -c;
+            float vy = -cg;
             if (lane == 0) vy += ay;
             const int lcode = (lane == last && fcode != kOutside && f < 32) ? fcode : kLeft;
             if (on && lcode != kUp) gyq[jk] = vy;
@@ -253,7 +321,7 @@ __global__ void __launch_bounds__(32) bwd_tile_kernel(const BwdArgs a)
             } else {
                 wj -= last + 1;  // the run continues to the left
             }
-            if (wj < c0 || wi < r0) break;
+            if (wj < c0 || wi < RT * max(0, ps0 - (wj - c0) / W)) break;  // left the band
         }
     }
 }
@@ -275,8 +343,8 @@ __global__ void grad_ref_reduce_kernel(const float* __restrict__ gyq, const int6
 template <int WB>
 cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 {
-    const int smem = bwd_smem_bytes(a.N, 32 * WB, a.R);
-    auto k = bwd_tile_kernel<WB>;
+    const int smem = bwd_smem_bytes(a.N, 4 * WB, a.RT);
+    auto k = bwd_band_kernel<WB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -287,31 +355,25 @@ cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 
 }  // namespace
 
-bool bwd_stride_supported(int K) { return K == 64 || K == 128 || K == 256; }
+bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
 
-// at least 64: the forward stages a checkpoint row per warp and needs the
-// 32 lanes' captures of one row to finish before lane 0 reaches the next
-bool bwd_row_stride_supported(int R) { return R == 64 || R == 128 || R == 256; }
-
-int bwd_smem_bytes(int N, int K, int R)
+int bwd_smem_bytes(int N, int W, int RT)
 {
-    const int word = K == 256 ? 2 : 1;
-    return 4 * (N + 2 * K + R) + R * 32 * word;
-}
-
-size_t ckpt_floats_per_query(int64_t N, int64_t M, int K, int R)
-{
-    // a column every K columns (N values each) and a row every R rows (M values each)
-    return static_cast<size_t>(N) * static_cast<size_t>(M / K) + static_cast<size_t>(N / R) * static_cast<size_t>(M);
+    // query samples, the window's samples and boundary column, and the
+    // choices of up to RT*kChunk + 7*RT + 32 steps of 32 lanes (W/2 bits each)
+    const int word = W <= 16 ? 1 : 2;
+    return 4 * (N + 8 * W + RT * kChunk) + (RT * kChunk + 7 * RT + 32) * 32 * word;
 }
 
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)
 {
     if (a.B <= 0) return cudaSuccess;
-    switch (a.K) {
-    case 64: return launch_walk_wb<2>(a, s);
-    case 128: return launch_walk_wb<4>(a, s);
-    case 256: return launch_walk_wb<8>(a, s);
+    if (a.K != 8 * a.W || (a.RT != 2 && a.RT != 4)) return cudaErrorInvalidValue;
+    switch (a.W) {
+    case 8: return launch_walk_wb<2>(a, s);
+    case 16: return launch_walk_wb<4>(a, s);
+    case 24: return launch_walk_wb<6>(a, s);
+    case 32: return launch_walk_wb<8>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

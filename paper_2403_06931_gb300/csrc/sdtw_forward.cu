@@ -46,12 +46,17 @@
 // sender's base and are converted on receipt; a sweep starts from base 0.  The
 // drift falls below 1e-7 and the worst error to ~1.5e-6.
 //
-// Optional checkpoints for the backward pass, taken as the wavefront passes
-// (a separate instantiation, so the plain forward carries none of it): a
-// thread whose strip ends at a multiple of K stores that column's absolute D
-// value for every row, and every thread stores its strip of every R-th row.
-// Both are staged in shared memory per warp and leave as whole 128-byte lines.
-// The backward recomputes R x K tiles from them.
+// Optional checkpoints for the backward pass (a separate instantiation, so the
+// plain forward carries none of it).  At the start of every chunk, right after
+// the rebase, every thread stores its state: the strip's latest row relative
+// to its base, the right-hand cells of its tile's other rows, its diagonal
+// input and the base.  Since thread l is one tile behind thread l-1, the rows
+// stored at one chunk start form an anti-diagonal staircase, the wavefront;
+// all lanes store on the same step, so the stores are whole-warp and
+// coalesced.  The strip whose first column is a multiple of K also stores the
+// left inputs it uses, already converted into its own base.  From a chunk's
+// wavefront and those columns the backward recomputes any K-column window of
+// the chunk with the forward's own operations, bit for bit.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -149,21 +154,6 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
     }
 }
 
-// Stage a strip of a checkpoint row: the lane's W values relative to its base,
-// with 16-byte stores, and the base (the flush adds it back).  Runs on a few
-// lanes at a time, so it is kept short.
-template <int W, typename V>
-__device__ __forceinline__ void stage_row(float* slot, const V (&prev)[W], float* base_slot, float B)
-{
-    static_assert(W % 4 == 0, "segment widths are multiples of 4");
-    float4* s4 = reinterpret_cast<float4*>(slot);
-#pragma unroll
-    for (int k = 0; k < W / 4; ++k)
-        s4[k] = make_float4(static_cast<float>(prev[4 * k]), static_cast<float>(prev[4 * k + 1]),
-                            static_cast<float>(prev[4 * k + 2]), static_cast<float>(prev[4 * k + 3]));
-    *base_slot = B;
-}
-
 // Register cap per segment width and tile height: the strip's samples and
 // previous row (2W), the tile's short-lived values and bookkeeping, leaving
 // room for several CTAs per SM.
@@ -196,42 +186,26 @@ fwd_chain_kernel(const FwdArgs a)
     const int S = blockDim.x * W;
     const int nsw = (M + S - 1) / S;
 
-    // shared memory: ring [P][kRing] and column buffer [Npad/RT] of edges; with
-    // checkpoints the staging areas; query samples [Npad] (zero padded);
-    // reduction scratch (value, index)[P].  Every part is 16-byte aligned.
-    const int nslot = CKPT ? 32 * W / a.K : 0;  // checkpoint lanes per warp
+    // shared memory: ring [P][kRing] and column buffer [Npad/RT] of edges;
+    // query samples [Npad] (zero padded); reduction scratch (value, index)[P].
+    // Every part is 16-byte aligned.
     E* ring = reinterpret_cast<E*>(smem_raw);
     E* colbuf = ring + P * kRing;
-    float* stage = reinterpret_cast<float*>(colbuf + Npad / RT);
-    // checkpoint staging: each warp gathers its 32 strips of a checkpoint row
-    // (values relative to each lane's base, and the bases) and its checkpoint
-    // lanes' column values of a chunk, so both leave as contiguous lines
-    float* rstage = stage + warp * 32 * W;                         // [P][32][W]
-    float* rbase = stage + (CKPT ? P * 32 * W : 0) + warp * 32;     // [P][32]
-    // column staging slots are RT*kChunk + 1 floats apart, so that the
-    // checkpoint lanes' simultaneous stores fall in different banks
-    constexpr int CS = RT * kChunk + 1;
-    float* cstage_all = stage + (CKPT ? P * 32 * (W + 1) : 0);      // [P][nslot][CS]
-    float* cstage = cstage_all + warp * nslot * CS;
-    V* xs = reinterpret_cast<V*>(cstage_all + (P * nslot * CS + 3) / 4 * 4);  // [Npad], 16-byte aligned
-    V* red_v = xs + Npad;                                                // [P]
-    int* red_i = reinterpret_cast<int*>(red_v + P);                      // [P]
+    V* xs = reinterpret_cast<V*>(colbuf + Npad / RT);  // [Npad]
+    V* red_v = xs + Npad;                              // [P]
+    int* red_i = reinterpret_cast<int*>(red_v + P);    // [P]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
 
-    const int64_t first_start = a.offsets ? a.offsets[a.q0] : static_cast<int64_t>(a.q0) * a.N;
     const int wlag = warp * (32 + kChunk);
     const int lag = wlag + lane;
     const int lag_last = (P - 1) * (32 + kChunk) + 31;
     const E* ring_in = ring + warp * kRing;
     E* ring_out = ring + (warp + 1) * kRing;
     const V INF = Md::inf();
-    // checkpoint rows: lanes reach a row on consecutive steps and reach the
-    // next one R/RT steps later, so rows are staged and written out per group
-    // of G = min(32, R/RT) lanes
-    const int G = CKPT ? min(32, a.R / RT) : 32;
-    const int logR = CKPT ? __ffs(a.R) - 1 : 0;  // R is a power of two
+    constexpr int EREC = fwd_record_floats(RT);  // floats of a thread's checkpoint record
+    const int L = blockDim.x;
 
     for (int it = 0;; ++it) {
         int q;
@@ -254,7 +228,6 @@ fwd_chain_kernel(const FwdArgs a)
             const int64_t stop = a.offsets[q + 1];
             const int64_t len = stop - start;
             bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total];
-            if (CKPT) bad = bad || start < first_start || (stop - first_start) > a.ckpt_rows;
             if (bad) {
                 if (threadIdx.x == 0) atomicOr(a.status, kStatusBadLength);
                 __syncthreads();
@@ -299,8 +272,10 @@ fwd_chain_kernel(const FwdArgs a)
         int p = -lag;   // tile of this thread's strip in sweep s (negative: not started)
         int s = 0;      // sweep
         int base = threadIdx.x * W;  // first column of the strip in sweep s
+        // checkpoints of this query: the wavefront slot and, for a strip that
+        // starts at a multiple of K, its boundary column
+        float* frq = CKPT ? a.fr + static_cast<int64_t>(q - a.q0) * a.fr_slot : nullptr;
         float* ck = nullptr;
-        float* rck = CKPT ? a.rowck + ((start - first_start) / a.R) * a.M : nullptr;
 
         for (int t0 = 0; t0 < total; t0 += kChunk) {
             if constexpr (Md::kRebase) {
@@ -316,6 +291,24 @@ fwd_chain_kernel(const FwdArgs a)
                 diag -= dl;
                 B = bn;
             }
+            if constexpr (CKPT) {
+                // the wavefront: the state after this thread's last tile, if it
+                // computed one (p == 0 of a later sweep still holds the previous
+                // sweep's last tile when the period has no idle steps)
+                if ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt)) {
+                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(t0 / kChunk) * L * (W + EREC)) +
+                                 threadIdx.x;
+#pragma unroll
+                    for (int k = 0; k < W / 4; ++k)
+                        f4[k * L] = make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]);
+                    if constexpr (RT == 2) {
+                        f4[(W / 4) * L] = make_float4(A[0][W - 1], diag, B, 0.f);
+                    } else {
+                        f4[(W / 4) * L] = make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag);
+                        f4[(W / 4 + 1) * L] = make_float4(B, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
             // fast path: no thread of this warp starts a sweep, idles or meets the
             // bottom row during the chunk (the test is uniform over the warp)
             const int gmin = t0 - wlag - 31;
@@ -328,8 +321,6 @@ fwd_chain_kernel(const FwdArgs a)
             if (fast) {
                 float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
                 if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
-                const int p_start = p;
-                float* cslot = (CKPT && ck) ? cstage + (((lane + 1) * W) / a.K - 1) * CS : nullptr;
 #pragma unroll 1
                 for (int u = 0; u < kChunk; ++u) {
                     const int t = t0 + u;
@@ -376,51 +367,15 @@ fwd_chain_kernel(const FwdArgs a)
                             colbuf[p] = e;
                     }
                     if constexpr (CKPT) {
-                        if (cslot) {
+                        if (ck) {
 #pragma unroll
-                            for (int rr = 0; rr < RT; ++rr)
-                                cslot[RT * u + rr] = static_cast<float>(rr < RT - 1 ? A[rr][W - 1] : prev[W - 1]) + B;
-                        }
-                        if ((((p + 1) * RT) & (a.R - 1)) == 0) stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
-                        // write out each group of G lanes once its last lane has staged
-                        const int pg = p + lane - (G - 1);  // tile of lane G-1 (same sweep here)
-                        if ((((pg + 1) * RT) & (a.R - 1)) == 0) {
-                            __syncwarp();
-                            const int col0 = s * S + warp * 32 * W;
-                            for (int g = 0; g < 32 / G; ++g) {
-                                // group g's lanes staged the row of tile pg - g*G
-                                const int m = (((pg - g * G) + 1) * RT >> logR) - 1;
-                                float* dst = rck + static_cast<int64_t>(m) * a.M + col0 + g * G * W;
-                                const float* src = rstage + g * G * W;
-                                const float* sb = rbase + g * G;
-                                const int lim = M - (col0 + g * G * W);
-                                for (int e = lane; e < G * W; e += 32)
-                                    if (e < lim) dst[e] = src[e] + sb[e / W];
-                            }
-                            __syncwarp();
+                            for (int rr = 0; rr < RT; ++rr) ck[RT * p + rr] = left[rr];
                         }
                     }
                     ++p;
                     // a one-warp chain reads and rewrites the column buffer less than
                     // a chunk apart: order those accesses within the warp
                     if (P == 1) __syncwarp();
-                }
-                if constexpr (CKPT) {
-                    if (nslot) {
-                        // the chunk's column checkpoints: RT*kChunk consecutive rows
-                        // per checkpoint lane, written as whole lines
-                        __syncwarp();
-                        float* dstl = ck ? ck + RT * p_start : nullptr;
-                        for (int j = 0; j < nslot; ++j) {
-                            const int src = ((j + 1) * a.K) / W - 1;
-                            float* d = reinterpret_cast<float*>(__shfl_sync(
-                                0xffffffffu, reinterpret_cast<unsigned long long>(dstl), src));
-                            if (d) {
-                                for (int e = lane; e < RT * kChunk; e += 32) d[e] = cstage[j * CS + e];
-                            }
-                        }
-                        __syncwarp();
-                    }
                 }
             } else {
 #pragma unroll 1
@@ -433,7 +388,6 @@ fwd_chain_kernel(const FwdArgs a)
                     float rb = 0.f;
                     if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
                     const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(nt) && s < nsw;
-                    bool rhit = false;
                     if (lane == 0) {
                         if (warp > 0) {
                             const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
@@ -465,11 +419,12 @@ fwd_chain_kernel(const FwdArgs a)
                             diag = Md::zero();
                             B = 0.f;
                             if constexpr (CKPT) {
+                                // a strip starting a K-column window (not the first)
+                                // keeps its left inputs for the backward
                                 ck = nullptr;
-                                const int edge = base + W;
-                                if (edge % a.K == 0 && edge / a.K <= a.nblk)
-                                    ck = a.ckpt + (start - first_start) * a.nblk +
-                                         static_cast<int64_t>(edge / a.K - 1) * n;
+                                if (base % a.K == 0 && base > 0 && base < M)
+                                    ck = a.colck + static_cast<int64_t>(q - a.q0) * a.ck_slot +
+                                         static_cast<int64_t>(base / a.K - 1) * N;
                             }
                         }
                         V left[RT];
@@ -497,38 +452,8 @@ fwd_chain_kernel(const FwdArgs a)
                             if (ck) {
 #pragma unroll
                                 for (int rr = 0; rr < RT; ++rr)
-                                    if (RT * p + rr < n)
-                                        ck[RT * p + rr] = static_cast<float>(rr < RT - 1 ? A[rr][W - 1] : prev[W - 1]) + B;
+                                    if (RT * p + rr < n) ck[RT * p + rr] = left[rr];
                             }
-                            if ((((p + 1) * RT) & (a.R - 1)) == 0 && RT * p + RT - 1 < n) {
-                                rhit = true;
-                                stage_row<W>(rstage + lane * W, prev, rbase + lane, B);
-                            }
-                        }
-                    }
-                    if constexpr (CKPT) {
-                        // write out each group of G lanes whose last lane staged just
-                        // now (lanes may straddle a sweep here: each group uses the
-                        // sweep and tile of its last lane)
-                        const unsigned hits = __ballot_sync(0xffffffffu, rhit);
-                        bool any = false;
-                        for (int g = G - 1; g < 32; g += G) any |= (hits >> g) & 1u;
-                        if (any) {
-                            __syncwarp();
-                            for (int g = 0; g < 32 / G; ++g) {
-                                const int gl = g * G + G - 1;  // the group's last lane
-                                const int sl = __shfl_sync(0xffffffffu, s, gl);
-                                const int pl = __shfl_sync(0xffffffffu, p, gl);
-                                if (!((hits >> gl) & 1u)) continue;
-                                const int col0 = sl * S + warp * 32 * W + g * G * W;
-                                const int m = ((pl + 1) * RT >> logR) - 1;
-                                float* dst = rck + static_cast<int64_t>(m) * a.M + col0;
-                                const float* src = rstage + g * G * W;
-                                const float* sb = rbase + g * G;
-                                for (int e = lane; e < G * W; e += 32)
-                                    if (col0 + e < M) dst[e] = src[e] + sb[e / W];
-                            }
-                            __syncwarp();
                         }
                     }
                     if (++p == Pp) {
@@ -567,6 +492,10 @@ fwd_chain_kernel(const FwdArgs a)
             }
             static_cast<V*>(a.cost)[q] = bv;
             a.end[q] = bc;
+            if constexpr (CKPT) {
+                a.ck_cost[q - a.q0] = bv;
+                a.ck_end[q - a.q0] = bc;
+            }
         }
         __syncthreads();
     }
@@ -638,19 +567,16 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 
 bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
 
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K, int RT)
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT)
 {
     // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
     // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
-    // 4-byte elements; with checkpoints (K > 0) the row staging [P][32][W], its
-    // bases [P][32] and the column staging [P][32W/K][RT*kChunk + 1] floats
-    // (rounded up to 16 bytes)
+    // 4-byte elements
     (void)dt;
+    (void)W;
     const int npad = (N + RT - 1) / RT * RT;
     const int esz = RT == 2 ? 16 : 32;
-    int bytes = esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
-    if (K > 0) bytes += 4 * P * (32 * W + 32) + 4 * ((P * (32 * W / K) * (RT * kChunk + 1) + 3) / 4 * 4);
-    return bytes;
+    return esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
@@ -661,6 +587,24 @@ int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
     const int64_t nt = (N + RT - 1) / RT;
     const int64_t Pp = std::max<int64_t>(nt, lag_last + kChunk);
     return (nsw - 1) * Pp + nt + lag_last;
+}
+
+int64_t fwd_chunks(int64_t M, int n, int W, int P, int RT)
+{
+    return (fwd_total_steps(M, n, W, P, RT) + kChunk - 1) / kChunk;
+}
+
+int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT)
+{
+    // the chunk count grows with the query length, so N bounds every query of
+    // a ragged batch
+    return fwd_chunks(M, N, W, P, RT) * 32 * P * (W + fwd_record_floats(RT));
+}
+
+int64_t ck_slot_floats(int64_t M, int N, int K)
+{
+    const int64_t windows = (M + K - 1) / K;
+    return (windows - 1) * static_cast<int64_t>(N);
 }
 
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt)
@@ -676,7 +620,7 @@ int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
 {
     if (plan.grid <= 0) return cudaSuccess;
-    return dispatch(dt, plan.W, plan.RT, a.ckpt != nullptr,
+    return dispatch(dt, plan.W, plan.RT, a.fr != nullptr,
                     [&](auto inst) { return decltype(inst)::launch(plan, a, s); });
 }
 

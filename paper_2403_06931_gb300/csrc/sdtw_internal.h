@@ -28,6 +28,7 @@ constexpr int kMaxWarpsPerQuery = 16;
 constexpr int kStatusBadLength = 1;  // a ragged query longer than N
 constexpr int kStatusBadEnd = 2;     // an end index outside [0, M)
 constexpr int kStatusTimeout = 4;    // a bounded wait ran out
+constexpr int kStatusReplay = 8;     // the backward's recompute missed the forward's cost at the end cell
 
 struct FwdArgs {
     const void* ref;
@@ -40,17 +41,25 @@ struct FwdArgs {
     int32_t B_total;  // queries in the whole batch (offsets has B_total + 1 entries)
     void* cost;
     int64_t* end;
-    // Checkpoints for the backward pass (nullptr: none), absolute D values:
-    //   ckpt   every K-th column: query q at (start_q - start_q0) * nblk, block b
-    //          (column (b+1)K-1) at b * n_q, one value per row;
-    //   rowck  every R-th row: query q at floor((start_q - start_q0) / R) * M,
-    //          stored row m (row (m+1)R-1) at m * M, one value per column.
-    float* ckpt;
-    float* rowck;
-    int32_t K;    // column checkpoint stride; a multiple of the segment width
-    int32_t R;    // row checkpoint stride; a power of two
-    int64_t nblk; // floor(M / K)
-    int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
+    // Checkpoints for the backward pass (fr == nullptr: none).  Query q of the
+    // launch uses slot q - q0 of every array below.
+    //   fr     the wavefront at the start of every chunk c of kChunk steps,
+    //          after the rebase: for thread tau, its strip's latest row (W
+    //          values relative to its base) as float4 [W/4][L], then its record
+    //          float4 [E/4][L] = {right-hand cells of its tile's other RT-1
+    //          rows, diag, base}; chunk c at c * L * (W + E); fr_slot floats
+    //          per query (E = fwd_record_floats(RT))
+    //   colck  the left inputs of the strip whose first column is bK (b >= 1),
+    //          in that strip's base: window b at (b - 1) * N, one per row;
+    //          ck_slot floats per query
+    //   ck_cost, ck_end  the query's cost and end column
+    float* fr;
+    int64_t fr_slot;
+    float* colck;
+    int64_t ck_slot;
+    int32_t K;    // window width: column checkpoint stride (8 W)
+    float* ck_cost;
+    int64_t* ck_end;
     int* status;
     int* queue;          // persistent mode: device work counter (reset to 0 before the launch)
     const int32_t* order;// persistent mode: query order (longest first), or nullptr
@@ -68,7 +77,7 @@ struct FwdPlan {
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int K, int RT);
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT);
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt);
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
@@ -87,22 +96,32 @@ struct BwdArgs {
     const float* grad_cost;
     float* grad_queries;
     int32_t* path;
-    const float* ckpt;   // column checkpoints of queries q0 .. q0+B-1 (layout as FwdArgs)
-    const float* rowck;  // row checkpoints (layout as FwdArgs)
-    int32_t K;           // tile columns: the column checkpoint stride
-    int32_t R;           // tile rows: the row checkpoint stride
-    int64_t nblk;
-    int64_t ckpt_rows;  // checkpoint capacity in query samples (from start_q0)
+    // checkpoints of queries q0 .. q0+B-1 (layout as FwdArgs) and the plan of
+    // the forward that wrote them
+    const float* fr;
+    int64_t fr_slot;
+    const float* colck;
+    int64_t ck_slot;
+    int32_t K;
+    const float* ck_cost;
+    const int64_t* ck_end;
+    int32_t W, P, RT;
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
     int64_t* span;   // [B][2] first and last column of each query's path
     int* status;
 };
 
+// Checkpoint geometry of a forward plan (sdtw_forward.cu): floats of one
+// thread's record, chunks of the wavefront schedule for a query of n rows, and
+// the per-query slot sizes of the two checkpoint arrays.
+__host__ __device__ constexpr int fwd_record_floats(int RT) { return RT == 2 ? 4 : 8; }
+int64_t fwd_chunks(int64_t M, int n, int W, int P, int RT);
+int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT);
+int64_t ck_slot_floats(int64_t M, int N, int K);
+
 // Backward launches (sdtw_backward.cu).
-bool bwd_stride_supported(int K);
-int bwd_smem_bytes(int N, int K, int R);
-size_t ckpt_floats_per_query(int64_t N, int64_t M, int K, int R);
-bool bwd_row_stride_supported(int R);
+bool bwd_width_supported(int W);
+int bwd_smem_bytes(int N, int W, int RT);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);

@@ -71,7 +71,7 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     plan.RT = 4;
     while (plan.P > 1 && static_cast<int64_t>(32) * (plan.P / 2) * plan.W >= M) plan.P /= 2;
     plan.block = 32 * plan.P;
-    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, 0, plan.RT);
+    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, plan.RT);
     plan.persistent = true;
     if (plan.smem > 227 * 1024) return SDTW_E_UNSUPPORTED;
     if (sdtw::fwd_total_steps(M, N, plan.W, plan.P, plan.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
@@ -100,11 +100,8 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     a.B_total = B;
     a.cost = cost;
     a.end = end;
-    a.ckpt = nullptr;
-    a.rowck = nullptr;
+    a.fr = nullptr;  // no checkpoints
     a.K = 1;
-    a.nblk = 0;
-    a.ckpt_rows = 0;
     a.status = scratch + kStatus;
     a.queue = scratch + kCounter;
     a.order = nullptr;

@@ -53,20 +53,24 @@ def main():
     if a.autotune:
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None
-    times = []
+    times, fwd_times = [], []
     for _ in range(a.reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
         cost, end = ctx.forward(ref, qs, offsets=offs, N=Nr)
+        e1.record()
         if a.backward:
             ctx.backward(ref, qs, end, torch.ones(w.B, device=dev), offsets=offs, N=Nr)
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        e2.record()
+        e2.synchronize()
+        times.append(e0.elapsed_time(e2))
+        fwd_times.append(e0.elapsed_time(e1))
     status = ctx.device_status()
     ms = sum(times) / len(times)
+    fms = sum(fwd_times) / len(fwd_times)
     print(json.dumps({"workload": w.name, "B": w.B, "N": N, "M": w.M, "dtype": a.dtype, "backward": a.backward,
                       "plan": ctx.plan(w.B, N, w.M, ragged=offs is not None), "ms": round(ms, 3),
+                      "fwd_ms": round(fms, 3), "bwd_ms": round(ms - fms, 3),
                       "gcups": round(w.cells / (ms * 1e-3) / 1e9, 2), "device_status": status}))
     ctx.close()
     if status != 0:

@@ -1,0 +1,486 @@
+"""CPU model of the backward checkpoints and of the backward's band replay.
+
+The checkpointing forward (csrc/sdtw_forward.cu) stores, at the start of every
+chunk of kChunk steps, the state of its wavefront: each thread's latest row
+(its strip of W columns, relative to the thread's integer base), the right-hand
+cells of its tile's other rows, its diagonal input and its base.  The rows a
+wavefront holds form an anti-diagonal staircase (thread l is one tile behind
+thread l-1), so these are checkpoints along anti-diagonals, one every kChunk
+steps.  Beside them, the strip that starts at every K-th column stores the left
+inputs it used (its boundary column, already converted into its own base).
+
+The backward (csrc/sdtw_backward.cu) recomputes one band at a time: the cells
+that the strips of one K-column window computed during one chunk, a
+parallelogram.  Starting from the chunk's stored wavefront and the window's
+stored boundary column, with the forward's own operations, it reproduces the
+forward's FP32 values bit for bit.
+
+This file replays both in plain Python with FP32 rounding (struct casts; the
+fused multiply-add is rounded once) and checks, on shapes with several warps,
+sweeps, ragged tails and both tile heights:
+
+* every cell of every band is reproduced exactly (value and base);
+* the band lookup used by the walk-back assigns every cell to one band whose
+  replay covers it;
+* a walk-back driven band by band from those replays follows the same path as
+  a walk over the whole FP32 matrix, and ends at the forward's cost.
+"""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+K_CHUNK = 32   # csrc/sdtw_internal.h kChunk
+INF = float("inf")
+
+
+def r32(v):
+    """Round a Python float to the nearest FP32 value (ties to even)."""
+    return struct.unpack("f", struct.pack("f", v))[0]
+
+
+def _next32(v, toward):
+    return float(np.nextafter(np.float32(v), np.float32(toward)))
+
+
+def fma32(a, b, c):
+    """a*b + c rounded once to FP32 (a, b, c FP32 values)."""
+    p = a * b                      # exact: two 24-bit significands
+    s = p + c
+    bb = s - p
+    e = (p - (s - bb)) + (c - bb)  # s + e == p + c exactly (TwoSum)
+    r = r32(s)
+    if r != s and e != 0.0:
+        o = _next32(r, INF if s > r else -INF)
+        if (r + o) / 2 == s:       # s is a tie between r and o: e decides
+            if (e > 0) == (o > r):
+                r = o
+    return r
+
+
+DIAG, LEFT, UP = 0, 1, 2
+
+
+def cell(xv, yv, up, dg, lf):
+    """(D, walk-back choice): the choice is read off the minimum by equality,
+    diagonal first, then left, then up (the walk-back's tie order)."""
+    d = r32(xv - yv)
+    m = min(up, dg, lf)
+    return fma32(d, d, m), (DIAG if m == dg else LEFT if m == lf else UP)
+
+
+class Plan:
+    def __init__(self, n, M, P, W, RT, K):
+        self.n, self.M, self.P, self.W, self.RT, self.K = n, M, P, W, RT, K
+        self.L = 32 * P
+        self.S = self.L * W
+        self.nsw = -(-M // self.S)
+        self.lag = [(t // 32) * (32 + K_CHUNK) + t % 32 for t in range(self.L)]
+        self.lag_last = self.lag[-1]
+        self.nt = -(-n // RT)
+        self.Pp = max(self.nt, self.lag_last + K_CHUNK)
+        self.total = (self.nsw - 1) * self.Pp + self.nt + self.lag_last
+        self.chunks = -(-self.total // K_CHUNK)
+
+    def band_of(self, i, j):
+        """(chunk, window) of the band holding cell (i, j)."""
+        s, tau = j // self.S, (j % self.S) // self.W
+        t = i // self.RT + self.lag[tau] + s * self.Pp
+        return t // K_CHUNK, j // self.K
+
+
+def model_forward(x, y, pl):
+    """FP32 model of the checkpointing forward: every cell (value, base), the
+    wavefront checkpoints, the boundary columns and (cost, end)."""
+    n, M, W, RT, K, L = pl.n, pl.M, pl.W, pl.RT, pl.K, pl.L
+    xs = [r32(v) for v in x] + [0.0] * (RT * pl.nt - n)
+    ys = [r32(v) for v in y]
+    prev = [[0.0] * W for _ in range(L)]
+    alast = [[0.0] * (RT - 1) for _ in range(L)]
+    diag = [0.0] * L
+    B = [0.0] * L
+    p = [-pl.lag[t] for t in range(L)]
+    s = [0] * L
+    base = [t * W for t in range(L)]
+    yv = [[0.0] * W for _ in range(L)]
+    ring, colbuf = {}, {}
+    frontier, colck, D = {}, {}, {}
+    best, best_col = INF, None
+    for t in range(pl.total):
+        if t % K_CHUNK == 0:
+            for tau in range(L):
+                bn = float(math.floor(r32(B[tau] + prev[tau][0])))
+                dl = r32(bn - B[tau])
+                prev[tau] = [r32(v - dl) for v in prev[tau]]
+                alast[tau] = [r32(v - dl) for v in alast[tau]]
+                diag[tau] = r32(diag[tau] - dl)
+                B[tau] = bn
+            c = t // K_CHUNK
+            for tau in range(L):
+                pp, ss = p[tau], s[tau]
+                if (1 <= pp <= pl.nt and ss < pl.nsw) or (pp == 0 and ss >= 1 and pl.Pp == pl.nt):
+                    frontier[(c, tau)] = (prev[tau][:], alast[tau][:], diag[tau], B[tau])
+        # the step's inputs: registers as they stand before anyone computes
+        recv, rb = [None] * L, [0.0] * L
+        for tau in range(L):
+            lane, w = tau % 32, tau // 32
+            act = 0 <= p[tau] < pl.nt and s[tau] < pl.nsw
+            if lane > 0:
+                recv[tau], rb[tau] = alast[tau - 1] + [prev[tau - 1][W - 1]], B[tau - 1]
+            elif w > 0:
+                recv[tau], rb[tau] = ring.get((w, t - K_CHUNK - 1), ([INF] * RT, 0.0))
+            elif act and s[tau] > 0:
+                recv[tau], rb[tau] = colbuf[p[tau]]
+            else:
+                recv[tau], rb[tau] = [INF] * RT, 0.0
+        for tau in range(L):
+            if not (0 <= p[tau] < pl.nt and s[tau] < pl.nsw):
+                continue
+            pt = p[tau]
+            if pt == 0:
+                base[tau] = s[tau] * pl.S + tau * W
+                yv[tau] = [ys[base[tau] + k] if base[tau] + k < M else 0.0 for k in range(W)]
+                prev[tau] = [0.0] * W
+                diag[tau] = 0.0
+                B[tau] = 0.0
+            dd = r32(rb[tau] - B[tau])
+            left = [r32(v + dd) for v in recv[tau]]
+            rows, codes, above, dg0 = [], [], prev[tau], diag[tau]
+            for rr in range(RT):
+                xv = xs[RT * pt + rr]
+                cur, cc = [], []
+                for j in range(W):
+                    up = above[j]
+                    dg = dg0 if j == 0 else above[j - 1]
+                    lf = left[rr] if j == 0 else cur[j - 1]
+                    v, code = cell(xv, yv[tau][j], up, dg, lf)
+                    cur.append(v)
+                    cc.append(code)
+                rows.append(cur)
+                codes.append(cc)
+                above, dg0 = cur, left[rr]
+            alast[tau] = [rows[rr][W - 1] for rr in range(RT - 1)]
+            prev[tau] = rows[RT - 1]
+            diag[tau] = left[RT - 1]
+            b0 = base[tau]
+            for rr in range(RT):
+                i = RT * pt + rr
+                if i >= n:
+                    continue
+                for j in range(W):
+                    if b0 + j < M:
+                        D[(i, b0 + j)] = (rows[rr][j], B[tau], codes[rr][j])
+                if b0 % K == 0 and 0 < b0 < M:
+                    colck[(b0 // K, i)] = left[rr]
+                if i == n - 1:
+                    for j in range(W):
+                        if b0 + j < M:
+                            v = r32(rows[rr][j] + B[tau])
+                            if v < best:
+                                best, best_col = v, b0 + j
+            if tau % 32 == 31:
+                e = (alast[tau] + [prev[tau][W - 1]], B[tau])
+                if tau // 32 < pl.P - 1:
+                    ring[(tau // 32 + 1, t)] = e
+                else:
+                    colbuf[pt] = e
+        for tau in range(L):
+            p[tau] += 1
+            if p[tau] == pl.Pp:
+                p[tau] = 0
+                s[tau] += 1
+    return {"D": D, "frontier": frontier, "colck": colck, "cost": best, "end": best_col, "x": xs, "y": ys}
+
+
+def model_replay(fw, pl, c, b):
+    """Recompute band (c, b) from its checkpoints, strip by strip, row by row
+    (the backward's replay, without its lane layout):
+    {(i, j): (value, base, walk-back choice)}."""
+    n, M, W, RT, K = pl.n, pl.M, pl.W, pl.RT, pl.K
+    c0 = b * K
+    s, tau0, nstrip = c0 // pl.S, (c0 % pl.S) // W, K // W
+    out = {}
+    info = []
+    for d in range(nstrip):
+        tau = tau0 + d
+        ps = c * K_CHUNK - pl.lag[tau] - s * pl.Pp
+        r0, r1 = RT * max(0, ps), min(n, RT * min(pl.nt, ps + K_CHUNK))
+        if ps > pl.nt:
+            info.append((ps, r0, r1, 0.0, None))   # finished before this chunk
+            continue
+        if ps >= 1:
+            # the strip's state after tile ps-1; with ps == nt its band is empty
+            # but its last tile's right-hand cells feed the next strip
+            pr, al, dg, Bd = fw["frontier"][(c, tau)]
+            edge = al + [pr[W - 1]]          # rows RT*(ps-1) .. RT*ps-1, last column
+        else:
+            pr, dg, Bd, edge = [0.0] * W, 0.0, 0.0, None
+        info.append((ps, r0, r1, Bd, edge))
+        cols = [c0 + d * W + k for k in range(W)]
+        yv = [fw["y"][j] if j < M else 0.0 for j in cols]
+        above = pr
+        for r in range(r0, r1):
+            if d == 0:
+                lf = INF if b == 0 else fw["colck"][(b, r)]
+            else:
+                ps_l, r0_l, _, B_l, edge_l = info[d - 1]
+                dd = r32(B_l - Bd)
+                if r >= r0_l:
+                    v = out[(r, c0 + d * W - 1)][0]
+                else:
+                    v = edge_l[r - RT * (ps_l - 1)]
+                lf = r32(v + dd)
+            cur = []
+            for k in range(W):
+                up = above[k]
+                dgk = dg if k == 0 else above[k - 1]
+                lfk = lf if k == 0 else cur[k - 1]
+                v, code = cell(fw["x"][r], yv[k], up, dgk, lfk)
+                cur.append(v)
+                out[(r, cols[k])] = (v, Bd, code)
+            above, dg = cur, lf
+    return out
+
+
+CASES = [
+    # (P, W, RT, n, M)
+    (2, 4, 2, 150, 700),    # two warps, three sweeps
+    (2, 4, 4, 151, 700),    # 4-row tiles, ragged last tile
+    (1, 8, 2, 70, 900),     # one warp, query shorter than the chain lag (padded period)
+    (2, 4, 4, 9, 333),      # tiny query
+    (3, 4, 2, 61, 1500),    # three warps, partial last sweep
+    (1, 4, 2, 160, 600),    # sweep period equal to the query's tiles (no idle steps)
+    (1, 4, 4, 299, 500),    # the same with 4-row tiles and a ragged last tile
+]
+
+
+def _setup(P, W, RT, n, M, seed):
+    rng = np.random.default_rng(seed)
+    y = np.cumsum(rng.standard_normal(M))
+    y = (y - y.mean()) / y.std()
+    o = int(rng.integers(0, max(1, M - n)))
+    x = y[o:o + n] if o + n <= M else rng.standard_normal(n)
+    x = x + 0.1 * rng.standard_normal(n)
+    x = (x - x.mean()) / (x.std() or 1.0)
+    pl = Plan(n, M, P, W, RT, 8 * W)
+    return pl, model_forward(x, y, pl)
+
+
+@pytest.mark.parametrize("P,W,RT,n,M", CASES)
+def test_band_replay_is_bit_exact(P, W, RT, n, M):
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 7 + M)
+    D = fw["D"]
+    assert len(D) == n * M
+    covered = {}
+    for c in range(pl.chunks):
+        for b in range(-(-M // pl.K)):
+            for key, val in model_replay(fw, pl, c, b).items():
+                if key[1] >= M:
+                    continue
+                assert key not in covered, f"cell {key} in bands {covered[key]} and {(c, b)}"
+                covered[key] = (c, b)
+                assert val == D[key], f"band {(c, b)} cell {key}: {val} != {D[key]}"
+    assert len(covered) == n * M
+    for (i, j), cb in covered.items():
+        assert pl.band_of(i, j) == cb
+
+
+def _walk(code_of, n, end):
+    """The walk-back from (n-1, end) following each cell's recorded choice;
+    column 0 goes up and the walk stops at row 0."""
+    i, j, path = n - 1, end, [(n - 1, end)]
+    while i > 0:
+        c = UP if j == 0 else code_of(i, j)
+        if c == DIAG:
+            i, j = i - 1, j - 1
+        elif c == LEFT:
+            j -= 1
+        else:
+            i -= 1
+        path.append((i, j))
+    return path
+
+
+@pytest.mark.parametrize("P,W,RT,n,M", CASES[:3])
+def test_walk_through_bands_matches_full_matrix(P, W, RT, n, M):
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 11 + M)
+    full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
+    cache = {}
+
+    def banded_code(i, j):
+        cb = pl.band_of(i, j)
+        if cb not in cache:
+            cache[cb] = model_replay(fw, pl, *cb)
+        return cache[cb][(i, j)][2]
+
+    banded = _walk(banded_code, n, fw["end"])
+    assert banded == full
+    assert len(cache) > 1
+    # the replay reaches the forward's cost at the end cell
+    v, Bv, _ = model_replay(fw, pl, *pl.band_of(n - 1, fw["end"]))[(n - 1, fw["end"])]
+    assert r32(v + Bv) == fw["cost"]
+
+
+# ---------------------------------------------------------------------------
+# The backward kernel's own schedule (csrc/sdtw_backward.cu bwd_band_kernel),
+# transliterated: the flat checkpoint layouts the forward writes, the warp's
+# 32 lanes (four per strip, W/4 columns each, lane l one row behind lane l-1),
+# the per-lane band bounds, and the cooperative walk with its band exits.
+
+def flat_checkpoints(fw, pl):
+    """The forward's checkpoint arrays in their device layouts (one query)."""
+    W, RT, L = pl.W, pl.RT, pl.L
+    E = 4 if RT == 2 else 8
+    fr = np.full(pl.chunks * L * (W + E), np.nan)
+    for (c, tau), (prev, alast, diag, B) in fw["frontier"].items():
+        base = c * L * (W + E)
+        for k in range(W // 4):                       # float4 [W/4][L]: prev
+            for e in range(4):
+                fr[base + (k * L + tau) * 4 + e] = prev[4 * k + e]
+        rec = (alast + [diag, B] + [0.0] * 8)[:E]     # float4 [E/4][L]: record
+        for e in range(E):
+            fr[base + ((W // 4 + e // 4) * L + tau) * 4 + e % 4] = rec[e]
+    nwin = -(-pl.M // pl.K)
+    ck = np.full(max(0, nwin - 1) * pl.n, np.nan)
+    for (b, i), v in fw["colck"].items():
+        ck[(b - 1) * pl.n + i] = v
+    return fr, ck
+
+
+def kernel_backward(fw, pl, end):
+    """The warp's walk from (n-1, end): (cells of the path, recomputed D at the
+    end cell, number of bands)."""
+    n, M, W, RT, L, S, Pp, nt = pl.n, pl.M, pl.W, pl.RT, pl.L, pl.S, pl.Pp, pl.nt
+    WB, KW, KC = W // 4, 32 * (W // 4), K_CHUNK
+    E = 4 if RT == 2 else 8
+    fr, ck = flat_checkpoints(fw, pl)
+    xs, ys_all = fw["x"], fw["y"]
+    lag = lambda tau: (tau >> 5) * (32 + KC) + (tau & 31)  # noqa: E731
+    wi, wj = n - 1, end
+    cells, first, v_end, bands = [], True, None, 0
+    done = False
+    while not done:
+        bands += 1
+        b = wj // KW
+        c0 = b * KW
+        s = c0 // S
+        tau0 = (c0 - s * S) // W
+        lag0 = lag(tau0)
+        dj = (wj - c0) // W
+        c = (wi // RT + lag0 + dj + s * Pp) // KC
+        ps0 = c * KC - lag0 - s * Pp
+        rtop = RT * (ps0 - 7)
+        assert RT * max(0, ps0 - dj) <= wi < min(n, RT * min(nt, ps0 - dj + KC)), "cell outside its band"
+        rf0 = RT * max(0, ps0)
+        re0 = min(min(n, RT * min(nt, ps0 + KC)), wi + 1)
+        ys = [ys_all[c0 + k] if c0 + k < M else 0.0 for k in range(KW)]
+        lcol = [ck[(b - 1) * n + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
+        frc = c * L * (W + E)
+        fr_at = lambda j, th: fr[frc + ((j >> 2) * L + th) * 4 + (j & 3)]             # noqa: E731
+        rec_at = lambda e, th: fr[frc + (((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]  # noqa: E731
+        lanes = []
+        for lane in range(32):
+            d, sub = lane >> 2, lane & 3
+            ps = ps0 - d
+            st = dict(d=d, sub=sub, ps=ps, rf=RT * max(0, ps), re=min(n, RT * min(nt, ps + KC)),
+                      rf_left=RT * max(0, ps + 1), e=[0.0] * 4, dd=0.0)
+            tau = tau0 + d
+            if 1 <= ps <= nt:
+                st["D"] = [fr_at(sub * WB + k, tau) for k in range(WB)]
+                st["B"] = rec_at(2 if RT == 2 else 4, tau)
+                st["dg"] = rec_at(RT - 1, tau) if sub == 0 else fr_at(sub * WB - 1, tau)
+            else:
+                st["D"], st["B"], st["dg"] = [0.0] * WB, 0.0, 0.0
+            if sub == 0 and d >= 1:
+                bsrc = 0.0
+                if 1 <= ps + 1 <= nt:
+                    if RT == 2:
+                        st["e"] = [rec_at(0, tau - 1), fr_at(W - 1, tau - 1), 0.0, 0.0]
+                    else:
+                        st["e"] = [rec_at(0, tau - 1), rec_at(1, tau - 1), rec_at(2, tau - 1), fr_at(W - 1, tau - 1)]
+                    bsrc = rec_at(2 if RT == 2 else 4, tau - 1)
+                st["dd"] = r32(bsrc - st["B"])
+            st["y"] = ys[lane * WB:(lane + 1) * WB]
+            lanes.append(st)
+        steps = wi - rtop + 32
+        dirs = {}
+        for sg in range(steps):
+            recv = [lanes[max(0, lane - 1)]["D"][WB - 1] for lane in range(32)]
+            for lane, st in enumerate(lanes):
+                r = sg + rtop - lane
+                if not (st["rf"] <= r < st["re"] and r <= wi):
+                    continue
+                if st["sub"] != 0:
+                    left = recv[lane]
+                elif st["d"] == 0:
+                    left = INF if b == 0 else lcol[r - rf0]
+                else:
+                    v = recv[lane] if r >= st["rf_left"] else st["e"][r - RT * st["ps"]]
+                    left = r32(v + st["dd"])
+                conv, code, dg = left, [], st["dg"]
+                for k in range(WB):
+                    up = st["D"][k]
+                    nv, cc = cell(xs[r], st["y"][k], up, dg, left)
+                    code.append(cc)
+                    dg, left = up, nv
+                    st["D"][k] = nv
+                st["dg"] = conv
+                dirs[(sg, lane)] = code
+        if first:
+            lj, kj = (wj - c0) // WB, (wj - c0) % WB
+            v_end = r32(lanes[lj]["D"][kj] + lanes[lj]["B"])
+            first = False
+        # the walk, 32 cells of a row at a time
+        while True:
+            if wi == 0:
+                cells.append((0, wj))
+                done = True
+                break
+            codes = []
+            for lane in range(32):
+                jk, code = wj - lane, 3
+                if jk >= c0:
+                    cc = jk - c0
+                    lam = cc // WB
+                    if wi >= RT * max(0, ps0 - (lam >> 2)):
+                        code = UP if jk == 0 else dirs[(wi - rtop + lam, lam)][cc - lam * WB]
+                codes.append(code)
+            f = next((k for k in range(32) if codes[k] != LEFT), 32)
+            fcode = codes[f] if f < 32 else LEFT
+            last = f - 1 if fcode == 3 else (f if f < 32 else 31)
+            cells.extend((wi, wj - k) for k in range(last + 1))
+            if f < 32 and fcode != 3:
+                jl = wj - last
+                wi -= 1
+                wj = jl - 1 if fcode == DIAG else jl
+            else:
+                wj -= last + 1
+            if wj < c0 or wi < RT * max(0, ps0 - (wj - c0) // W):
+                break
+    # a cell of a row can be listed twice (the row's end and the next start)
+    out = []
+    for cl in cells:
+        if not out or out[-1] != cl:
+            out.append(cl)
+    return out, v_end, bands
+
+
+KERNEL_CASES = [
+    # (P, W, RT, n, M): the kernel's windows are 8 strips of W columns
+    (2, 4, 2, 150, 700),
+    (2, 4, 4, 151, 700),
+    (1, 8, 2, 70, 900),
+    (1, 4, 4, 299, 500),
+    (2, 8, 4, 97, 1300),
+]
+
+
+@pytest.mark.parametrize("P,W,RT,n,M", KERNEL_CASES)
+def test_kernel_band_schedule_and_walk(P, W, RT, n, M):
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 13 + M)
+    cells, v_end, bands = kernel_backward(fw, pl, fw["end"])
+    assert v_end == fw["cost"]
+    full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
+    assert cells == full
+    assert bands > 1

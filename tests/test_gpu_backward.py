@@ -129,32 +129,35 @@ def test_walkback_tie_rule_on_many_queries(gpu):
     assert same >= 5 and matched >= 0.5 * total
 
 
-@pytest.mark.parametrize("B,N,M,K,R", [(4, 50, 700, 64, 64), (3, 300, 2000, 128, 64), (2, 129, 5000, 256, 64),
-                                       (3, 1, 300, 64, 256), (2, 40, 1, 64, 64), (2, 700, 600, 128, 128),
-                                       (2, 600, 3000, 256, 256), (3, 257, 1100, 256, 64)])
-def test_backward_shapes(gpu, B, N, M, K, R):
+@pytest.mark.parametrize("B,N,M,W,RT,P", [(4, 50, 700, 8, 2, 1), (3, 300, 2000, 16, 4, 2), (2, 129, 5000, 32, 2, 4),
+                                          (3, 1, 300, 8, 4, 2), (2, 40, 1, 8, 2, 1), (2, 700, 600, 16, 2, 1),
+                                          (2, 600, 3000, 24, 4, 4), (3, 257, 1100, 24, 2, 3),
+                                          (2, 1000, 40000, 24, 4, 4), (2, 333, 20000, 32, 4, 8)])
+def test_backward_shapes(gpu, B, N, M, W, RT, P):
+    # band replays across warps, sweeps, ragged last tiles, a one-row query,
+    # a one-column reference and queries longer than the reference
     w = inputs.tiny(B=B, N=N, M=M, seed=500 + B + N + M)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=K, ckpt_row_stride=R)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=P)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     gy_sum = check_validity(w, cost, end, gq, gr, path, g, range(B), oc)
     assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
 
 
 @pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 16, 32])
+@pytest.mark.parametrize("W", [8, 16, 24, 32])
 def test_backward_every_tile_height_and_width(gpu, RT, W):
-    # checkpoints taken by every forward variant: rows staged in groups (RT = 4, R = 64)
+    # checkpoints taken by every checkpointing forward variant
     w = inputs.tiny(B=3, N=700, M=9000, seed=400 + RT + W)
     cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=2)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
 
-def test_backward_long_vertical_runs_cross_windows(gpu):
+def test_backward_long_vertical_runs_cross_bands(gpu):
     # a query far longer than the reference forces long vertical runs, so the
-    # walk climbs many rows inside one block (several direction-code windows)
+    # walk climbs through many bands of one window
     w = inputs.tiny(B=2, N=2500, M=300, seed=61)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=64, ckpt_row_stride=64)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=8, tile_rows=2, warps_per_query=1)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
@@ -167,17 +170,34 @@ def test_backward_ragged(gpu):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
 
 
+def _ckpt_floats_per_query(M, N, W, P, RT):
+    """Backward workspace per query (floats) of a checkpointing plan: the
+    wavefront slot (one record of W + 4 or W + 8 floats per thread and chunk of
+    32 steps), the boundary columns every 8 W columns, a gradient row and 7
+    scalars (the layout the library documents)."""
+    S, lag_last = 32 * P * W, (P - 1) * 64 + 31
+    nsw, nt = -(-M // S), -(-N // RT)
+    total = (nsw - 1) * max(nt, lag_last + 32) + nt + lag_last
+    fr = -(-total // 32) * 32 * P * (W + (4 if RT == 2 else 8))
+    ck = (-(-M // (8 * W)) - 1) * N
+    return fr + ck + M + 7
+
+
 def test_chunked_and_recomputed_backward_are_identical(gpu):
     w = inputs.tiny(B=9, N=200, M=4000, seed=81)
-    st = dict(ckpt_stride=256, ckpt_row_stride=64)
+    st = dict(seg_width=16, tile_rows=4, warps_per_query=2)
     a = run_bwd(gpu, w, keep=True, **st)                          # checkpoints from the forward
     b = run_bwd(gpu, w, keep=False, **st)                         # backward re-runs the forward
-    # per query: a column every 256 columns, a row every 64 rows, one gradient row, span
-    per_q = 4 * (200 * (4000 // 256) + (200 // 64) * 4000) + 4 * 4000 + 32
-    c = run_bwd(gpu, w, keep=False, mem_cap_bytes=4 * per_q + 20_000, **st)   # forces chunks of 4 queries
+    # a cap that holds the checkpoints of 4 queries: chunks of 4, 4 and 1
+    fixed = 8 + 4 * w.B + 12 * w.B
+    per_q = _ckpt_floats_per_query(w.M, w.N, 16, 2, 4)
+    c = run_bwd(gpu, w, keep=False, mem_cap_bytes=fixed + 4 * (4 * per_q + 32) + 8, **st)
     for u, v in ((a, b), (a, c)):
         for k in range(5):
             assert np.array_equal(u[k], v[k])
+    # too small a cap for one query fails at creation
+    with pytest.raises(capi.SdtwError):
+        run_bwd(gpu, w, keep=False, mem_cap_bytes=fixed + 4 * per_q // 2, **st)
 
 
 def test_host_forward_backward_matches_device(gpu):
