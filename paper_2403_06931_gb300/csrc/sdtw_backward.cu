@@ -8,10 +8,11 @@
 //   d cost / d y_j = sum over the path's cells in column j of -2 (x_i - y_j).
 //
 // The n x M matrix is never stored.  The checkpointing forward left, at the
-// start of every chunk of kChunk steps, its wavefront (each thread's latest
+// end of every chunk of kChunk steps, its wavefront (each thread's latest
 // row, the right-hand cells of its tile's other rows, its diagonal input and
-// its integer base: an anti-diagonal staircase of rows), and the left inputs
-// of every strip that starts a K-column window (K = 8 W).  The cells that the
+// its integer base: an anti-diagonal staircase of rows, stored before the
+// next chunk's rebase, which is redone here), and the left inputs of every
+// strip that starts a K-column window (K = 8 W).  The cells that the
 // eight strips of one window computed during one chunk form a band, a
 // parallelogram (each strip one tile higher than its left neighbour).  The
 // walk proceeds band by band, one warp per query:
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     float* xs = reinterpret_cast<float*>(smem_raw);  // [N] query samples
     float* ys = xs + N;                              // [KW] reference samples of the window
     float* lcol = ys + KW;                           // [RT*kChunk] the window's boundary column
-    DW* dirs = reinterpret_cast<DW*>(lcol + RT * kChunk);  // [steps][32] walk-back choices
+    DW* dirs = reinterpret_cast<DW*>(lcol + RT * kChunk);  // [2*steps][32] walk-back choices (two masks)
 
     int64_t start;
     int n;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         __syncwarp();
         for (int k = lane; k < KW; k += 32) ys[k] = c0 + k < M ? a.ref[c0 + k] : 0.f;
         if (b > 0)
-            for (int k = lane; k < re0 - rf0; k += 32) lcol[k] = ckq[static_cast<int64_t>(b - 1) * N + rf0 + k];
+            for (int k = lane; k < re0 - rf0; k += 32) lcol[k] = ckq[static_cast<int64_t>(b - 1) * ck_rows(N) + rf0 + k];
 
         // ---- the lane's starting state: the chunk's wavefront, or the virtual
         // zero row -1 for a strip that starts its sweep inside the chunk
@@ -183,13 +184,21 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         const int tau = tau0 + d;
         auto fr_at = [&](int j, int th) { return frc[((j >> 2) * L + th) * 4 + (j & 3)]; };
         auto rec_at = [&](int e, int th) { return frc[(((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]; };
+        // the forward stored its state before the chunk's rebase: redo it
+        // (new base: the integer part of the strip's first column)
+        auto rebase = [&](int th, float& bn, float& dl) {
+            const float b0 = rec_at(RT == 2 ? 2 : 4, th);
+            bn = floorf(b0 + fr_at(0, th));
+            dl = bn - b0;
+        };
         float D[WB], y[WB];
         float Bl = 0.f, dg = 0.f;
         if (ps >= 1 && ps <= nt) {
+            float dl;
+            rebase(tau, Bl, dl);
 #pragma unroll
-            for (int k = 0; k < WB; ++k) D[k] = fr_at(sub * WB + k, tau);
-            Bl = rec_at(RT == 2 ? 2 : 4, tau);
-            dg = sub == 0 ? rec_at(RT - 1, tau) : fr_at(sub * WB - 1, tau);
+            for (int k = 0; k < WB; ++k) D[k] = fr_at(sub * WB + k, tau) - dl;
+            dg = (sub == 0 ? rec_at(RT - 1, tau) : fr_at(sub * WB - 1, tau)) - dl;
         } else {
 #pragma unroll
             for (int k = 0; k < WB; ++k) D[k] = 0.f;
@@ -200,15 +209,16 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         if (sub == 0 && d >= 1) {
             float Bsrc = 0.f;
             if (ps + 1 >= 1 && ps + 1 <= nt) {
-                e0 = rec_at(0, tau - 1);
+                float dl;
+                rebase(tau - 1, Bsrc, dl);
+                e0 = rec_at(0, tau - 1) - dl;
                 if (RT == 2) {
-                    e1 = fr_at(W - 1, tau - 1);
+                    e1 = fr_at(W - 1, tau - 1) - dl;
                 } else {
-                    e1 = rec_at(1, tau - 1);
-                    e2 = rec_at(2, tau - 1);
-                    e3 = fr_at(W - 1, tau - 1);
+                    e1 = rec_at(1, tau - 1) - dl;
+                    e2 = rec_at(2, tau - 1) - dl;
+                    e3 = fr_at(W - 1, tau - 1) - dl;
                 }
-                Bsrc = rec_at(RT == 2 ? 2 : 4, tau - 1);
             }
             dd = Bsrc - Bl;
         }
@@ -216,42 +226,72 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
 #pragma unroll
         for (int k = 0; k < WB; ++k) y[k] = ys[lane * WB + k];
 
-        // ---- recompute the band's rows down to row wi, recording choices
-        const int steps = wi - rtop + 32;
+        // ---- recompute the band's rows down to row wi, recording choices.
+        // Lane l handles rows r and r+1 (r - rtop even) at step (r - rtop)/2 + l:
+        // the two rows are two dependency chains, row r+1 one column behind.
+        const int steps = (wi - rtop) / 2 + 32;
+        const int hi = min(re, wi + 1);  // this lane's rows end here
+        float lastA = 0.f, lastB = 0.f;  // right-hand cells of the lane's previous row pair
         for (int sg = 0; sg < steps; ++sg) {
-            const float recv = __shfl_up_sync(0xffffffffu, D[WB - 1], 1);
-            const int r = sg + rtop - lane;
-            if (r >= rf && r < re && r <= wi) {
-                float left;
+            const float recvA = __shfl_up_sync(0xffffffffu, lastA, 1);
+            const float recvB = __shfl_up_sync(0xffffffffu, lastB, 1);
+            const int r = rtop + 2 * (sg - lane);
+            if (r >= rf && r < hi) {
+                const bool vb = r + 1 < hi;  // row r+1 is in the band (else: last row)
+                float lA, lB;
                 if (sub != 0) {
-                    left = recv;  // same strip, same base
+                    lA = recvA;  // same strip, same base
+                    lB = recvB;
                 } else if (d == 0) {
-                    left = b == 0 ? INF : lcol[r - rf0];  // already in this strip's base
+                    lA = b == 0 ? INF : lcol[r - rf0];  // already in this strip's base
+                    lB = (b == 0 || !vb) ? INF : lcol[r + 1 - rf0];
                 } else {
-                    float v = recv;
+                    float vA = recvA, vB = recvB;
                     if (r < rf_left) {
+                        // the left strip's last tile before the band (rows RT*ps ..)
                         const int e = r - RT * ps;
-                        v = e == 0 ? e0 : e == 1 ? e1 : e == 2 ? e2 : e3;
+                        vA = e == 0 ? e0 : e2;
+                        vB = e == 0 ? e1 : e3;
                     }
-                    left = v + dd;  // into this strip's base, as the forward converts
+                    lA = vA + dd;  // into this strip's base, as the forward converts
+                    lB = vB + dd;
                 }
-                const float xv = xs[r];
-                const float conv = left;
-                uint32_t code = 0;
+                const float xA = xs[r];
+                const float xB = vb ? xs[r + 1] : 0.f;
+                const float convA = lA, convB = lB;
+                float dgA = dg, dgB = lA;
+                // walk-back choices as two masks per row: bit k of nd is set
+                // unless the minimum is the diagonal; bit k of nu is set when it
+                // is neither the diagonal nor the left cell (the cell above)
+                uint32_t ndA = 0, nuA = 0, ndB = 0, nuB = 0;
 #pragma unroll
                 for (int k = 0; k < WB; ++k) {
                     const float up = D[k];
-                    const float v = min3_f32(up, dg, left);
-                    const uint32_t cc = v == dg ? kDiag : (v == left ? kLeft : kUp);
-                    const float dlt = xv - y[k];
-                    const float nv = fmaf(dlt, dlt, v);
-                    code |= cc << (2 * k);
-                    dg = up;
-                    left = nv;
-                    D[k] = nv;
+                    const float vA = min3_f32(up, dgA, lA);
+                    if (vA != dgA) {
+                        ndA |= 1u << k;
+                        if (vA != lA) nuA |= 1u << k;
+                    }
+                    const float tA = xA - y[k];
+                    const float nA = fmaf(tA, tA, vA);
+                    dgA = up;
+                    lA = nA;
+                    const float vB = min3_f32(nA, dgB, lB);
+                    if (vB != dgB) {
+                        ndB |= 1u << k;
+                        if (vB != lB) nuB |= 1u << k;
+                    }
+                    const float tB = xB - y[k];
+                    const float nB = fmaf(tB, tB, vB);
+                    dgB = nA;
+                    lB = nB;
+                    D[k] = vb ? nB : nA;
                 }
-                dg = conv;
-                dirs[sg * 32 + lane] = static_cast<DW>(code);
+                lastA = lA;
+                lastB = lB;
+                dg = vb ? convB : convA;
+                dirs[(2 * sg) * 32 + lane] = static_cast<DW>(ndA | (nuA << WB));
+                dirs[(2 * sg + 1) * 32 + lane] = static_cast<DW>(ndB | (nuB << WB));
             }
         }
 
@@ -290,7 +330,12 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
             if (jk >= c0) {
                 const int cc = jk - c0, lam = cc / WB;
                 if (wi >= RT * max(0, ps0 - (lam >> 2))) {  // row wi is in the band in that strip
-                    code = jk == 0 ? kUp : (dirs[(wi - rtop + lam) * 32 + lam] >> (2 * (cc - lam * WB))) & 3;
+                    if (jk == 0) {
+                        code = kUp;
+                    } else {
+                        const uint32_t m = dirs[(wi - rtop + 2 * lam) * 32 + lam] >> (cc - lam * WB);
+                        code = !(m & 1u) ? kDiag : ((m >> WB) & 1u) ? kUp : kLeft;
+                    }
                 }
             }
             const unsigned stop = __ballot_sync(0xffffffffu, code != kLeft);
@@ -360,9 +405,9 @@ bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 24 || W == 32
 int bwd_smem_bytes(int N, int W, int RT)
 {
     // query samples, the window's samples and boundary column, and the
-    // choices of up to RT*kChunk + 7*RT + 32 steps of 32 lanes (W/2 bits each)
+    // choices of up to RT*kChunk + 7*RT + 64 rows of 32 lanes (W/2 bits each)
     const int word = W <= 16 ? 1 : 2;
-    return 4 * (N + 8 * W + RT * kChunk) + (RT * kChunk + 7 * RT + 32) * 32 * word;
+    return 4 * (N + 8 * W + RT * kChunk) + (RT * kChunk + 7 * RT + 64) * 32 * word;
 }
 
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)

@@ -154,6 +154,19 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
     }
 }
 
+// The RT left inputs of a tile as one vector store (the destination is
+// 4 * RT-byte aligned: windows are ck_rows(N) floats apart).  Checkpoints are
+// written once and read by a later kernel, so they are stored with the
+// streaming (evict-first) hint: plain stores measurably slowed the fill.
+template <int RT>
+__device__ __forceinline__ void store_rows(float* dst, const float (&v)[RT])
+{
+    if constexpr (RT == 2)
+        __stcs(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
+    else
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+}
+
 // Register cap per segment width and tile height: the strip's samples and
 // previous row (2W), the tile's short-lived values and bookkeeping, leaving
 // room for several CTAs per SM.
@@ -291,24 +304,6 @@ fwd_chain_kernel(const FwdArgs a)
                 diag -= dl;
                 B = bn;
             }
-            if constexpr (CKPT) {
-                // the wavefront: the state after this thread's last tile, if it
-                // computed one (p == 0 of a later sweep still holds the previous
-                // sweep's last tile when the period has no idle steps)
-                if ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt)) {
-                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(t0 / kChunk) * L * (W + EREC)) +
-                                 threadIdx.x;
-#pragma unroll
-                    for (int k = 0; k < W / 4; ++k)
-                        f4[k * L] = make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]);
-                    if constexpr (RT == 2) {
-                        f4[(W / 4) * L] = make_float4(A[0][W - 1], diag, B, 0.f);
-                    } else {
-                        f4[(W / 4) * L] = make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag);
-                        f4[(W / 4 + 1) * L] = make_float4(B, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
             // fast path: no thread of this warp starts a sweep, idles or meets the
             // bottom row during the chunk (the test is uniform over the warp)
             const int gmin = t0 - wlag - 31;
@@ -367,10 +362,7 @@ fwd_chain_kernel(const FwdArgs a)
                             colbuf[p] = e;
                     }
                     if constexpr (CKPT) {
-                        if (ck) {
-#pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) ck[RT * p + rr] = left[rr];
-                        }
+                        if (ck) store_rows<RT>(ck + RT * p, left);
                     }
                     ++p;
                     // a one-warp chain reads and rewrites the column buffer less than
@@ -424,7 +416,7 @@ fwd_chain_kernel(const FwdArgs a)
                                 ck = nullptr;
                                 if (base % a.K == 0 && base > 0 && base < M)
                                     ck = a.colck + static_cast<int64_t>(q - a.q0) * a.ck_slot +
-                                         static_cast<int64_t>(base / a.K - 1) * N;
+                                         static_cast<int64_t>(base / a.K - 1) * ck_rows(N);
                             }
                         }
                         V left[RT];
@@ -449,11 +441,7 @@ fwd_chain_kernel(const FwdArgs a)
                                 colbuf[p] = e;
                         }
                         if constexpr (CKPT) {
-                            if (ck) {
-#pragma unroll
-                                for (int rr = 0; rr < RT; ++rr)
-                                    if (RT * p + rr < n) ck[RT * p + rr] = left[rr];
-                            }
+                            if (ck) store_rows<RT>(ck + RT * p, left);  // padding rows fall in the padded slot
                         }
                     }
                     if (++p == Pp) {
@@ -461,6 +449,26 @@ fwd_chain_kernel(const FwdArgs a)
                         ++s;
                     }
                     if (P == 1) __syncwarp();
+                }
+            }
+            if constexpr (CKPT) {
+                // the wavefront as this chunk leaves it (the state at the start
+                // of the next chunk, before its rebase), if this thread has
+                // computed a tile (p == 0 of a later sweep still holds the
+                // previous sweep's last tile when the period has no idle steps)
+                const int c1 = t0 / kChunk + 1;
+                if (t0 + kChunk < total && ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt))) {
+                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(c1) * L * (W + EREC)) +
+                                 threadIdx.x;
+#pragma unroll
+                    for (int k = 0; k < W / 4; ++k)
+                        __stcs(f4 + k * L, make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]));
+                    if constexpr (RT == 2) {
+                        __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], diag, B, 0.f));
+                    } else {
+                        __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag));
+                        __stcs(f4 + (W / 4 + 1) * L, make_float4(B, 0.f, 0.f, 0.f));
+                    }
                 }
             }
             __syncthreads();
@@ -604,7 +612,7 @@ int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT)
 int64_t ck_slot_floats(int64_t M, int N, int K)
 {
     const int64_t windows = (M + K - 1) / K;
-    return (windows - 1) * static_cast<int64_t>(N);
+    return (windows - 1) * static_cast<int64_t>(ck_rows(N));
 }
 
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt)

@@ -44,13 +44,14 @@ struct FwdArgs {
     // Checkpoints for the backward pass (fr == nullptr: none).  Query q of the
     // launch uses slot q - q0 of every array below.
     //   fr     the wavefront at the start of every chunk c of kChunk steps,
-    //          after the rebase: for thread tau, its strip's latest row (W
-    //          values relative to its base) as float4 [W/4][L], then its record
-    //          float4 [E/4][L] = {right-hand cells of its tile's other RT-1
-    //          rows, diag, base}; chunk c at c * L * (W + E); fr_slot floats
-    //          per query (E = fwd_record_floats(RT))
+    //          before that chunk's rebase: for thread tau, its strip's latest
+    //          row (W values relative to its base) as float4 [W/4][L], then
+    //          its record float4 [E/4][L] = {right-hand cells of its tile's
+    //          other RT-1 rows, diag, base}; chunk c at c * L * (W + E);
+    //          fr_slot floats per query (E = fwd_record_floats(RT))
     //   colck  the left inputs of the strip whose first column is bK (b >= 1),
-    //          in that strip's base: window b at (b - 1) * N, one per row;
+    //          in that strip's base: window b at (b - 1) * ck_rows(N), one per
+    //          row (tiles past the query's end included);
     //          ck_slot floats per query
     //   ck_cost, ck_end  the query's cost and end column
     float* fr;
@@ -115,6 +116,7 @@ struct BwdArgs {
 // thread's record, chunks of the wavefront schedule for a query of n rows, and
 // the per-query slot sizes of the two checkpoint arrays.
 __host__ __device__ constexpr int fwd_record_floats(int RT) { return RT == 2 ? 4 : 8; }
+__host__ __device__ constexpr int ck_rows(int N) { return (N + 3) / 4 * 4; }
 int64_t fwd_chunks(int64_t M, int n, int W, int P, int RT);
 int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT);
 int64_t ck_slot_floats(int64_t M, int N, int K);

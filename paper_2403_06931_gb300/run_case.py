@@ -23,7 +23,7 @@ def main():
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--M", type=int, default=None)
     ap.add_argument("--dtype", default="f32", choices=["f32", "i8"])
-    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=3, help="timed runs after one warm-up")
     ap.add_argument("--backward", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--seg-width", type=int, default=0)
@@ -54,7 +54,7 @@ def main():
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None
     times, fwd_times = [], []
-    for _ in range(a.reps):
+    for rep in range(a.reps + 1):  # the first run is an untimed warm-up
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
         cost, end = ctx.forward(ref, qs, offsets=offs, N=Nr)
@@ -63,8 +63,9 @@ def main():
             ctx.backward(ref, qs, end, torch.ones(w.B, device=dev), offsets=offs, N=Nr)
         e2.record()
         e2.synchronize()
-        times.append(e0.elapsed_time(e2))
-        fwd_times.append(e0.elapsed_time(e1))
+        if rep > 0:
+            times.append(e0.elapsed_time(e2))
+            fwd_times.append(e0.elapsed_time(e1))
     status = ctx.device_status()
     ms = sum(times) / len(times)
     fms = sum(fwd_times) / len(fwd_times)

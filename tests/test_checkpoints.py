@@ -1,9 +1,10 @@
 """CPU model of the backward checkpoints and of the backward's band replay.
 
-The checkpointing forward (csrc/sdtw_forward.cu) stores, at the start of every
+The checkpointing forward (csrc/sdtw_forward.cu) stores, at the end of every
 chunk of kChunk steps, the state of its wavefront: each thread's latest row
 (its strip of W columns, relative to the thread's integer base), the right-hand
-cells of its tile's other rows, its diagonal input and its base.  The rows a
+cells of its tile's other rows, its diagonal input and its base, as they stand
+before the next chunk's rebase (the backward redoes that rebase).  The rows a
 wavefront holds form an anti-diagonal staircase (thread l is one tile behind
 thread l-1), so these are checkpoints along anti-diagonals, one every kChunk
 steps.  Beside them, the strip that starts at every K-th column stores the left
@@ -70,6 +71,20 @@ def cell(xv, yv, up, dg, lf):
     return fma32(d, d, m), (DIAG if m == dg else LEFT if m == lf else UP)
 
 
+def rebase(B, first):
+    """A thread's new integer base at a chunk start and the shift applied to
+    its values (the forward's rebase, replayed by the backward)."""
+    bn = float(math.floor(r32(B + first)))
+    return bn, r32(bn - B)
+
+
+def frontier_state(fw, c, tau):
+    """A thread's state at the start of chunk c, after the rebase."""
+    prev, alast, diag, B = fw["frontier"][(c, tau)]
+    bn, dl = rebase(B, prev[0])
+    return [r32(v - dl) for v in prev], [r32(v - dl) for v in alast], r32(diag - dl), bn
+
+
 class Plan:
     def __init__(self, n, M, P, W, RT, K):
         self.n, self.M, self.P, self.W, self.RT, self.K = n, M, P, W, RT, K
@@ -109,18 +124,18 @@ def model_forward(x, y, pl):
     best, best_col = INF, None
     for t in range(pl.total):
         if t % K_CHUNK == 0:
-            for tau in range(L):
-                bn = float(math.floor(r32(B[tau] + prev[tau][0])))
-                dl = r32(bn - B[tau])
-                prev[tau] = [r32(v - dl) for v in prev[tau]]
-                alast[tau] = [r32(v - dl) for v in alast[tau]]
-                diag[tau] = r32(diag[tau] - dl)
-                B[tau] = bn
+            # the wavefront as the previous chunk left it (before the rebase)
             c = t // K_CHUNK
             for tau in range(L):
                 pp, ss = p[tau], s[tau]
                 if (1 <= pp <= pl.nt and ss < pl.nsw) or (pp == 0 and ss >= 1 and pl.Pp == pl.nt):
                     frontier[(c, tau)] = (prev[tau][:], alast[tau][:], diag[tau], B[tau])
+            for tau in range(L):
+                bn, dl = rebase(B[tau], prev[tau][0])
+                prev[tau] = [r32(v - dl) for v in prev[tau]]
+                alast[tau] = [r32(v - dl) for v in alast[tau]]
+                diag[tau] = r32(diag[tau] - dl)
+                B[tau] = bn
         # the step's inputs: registers as they stand before anyone computes
         recv, rb = [None] * L, [0.0] * L
         for tau in range(L):
@@ -212,7 +227,7 @@ def model_replay(fw, pl, c, b):
         if ps >= 1:
             # the strip's state after tile ps-1; with ps == nt its band is empty
             # but its last tile's right-hand cells feed the next strip
-            pr, al, dg, Bd = fw["frontier"][(c, tau)]
+            pr, al, dg, Bd = frontier_state(fw, c, tau)
             edge = al + [pr[W - 1]]          # rows RT*(ps-1) .. RT*ps-1, last column
         else:
             pr, dg, Bd, edge = [0.0] * W, 0.0, 0.0, None
@@ -342,9 +357,10 @@ def flat_checkpoints(fw, pl):
         for e in range(E):
             fr[base + ((W // 4 + e // 4) * L + tau) * 4 + e % 4] = rec[e]
     nwin = -(-pl.M // pl.K)
-    ck = np.full(max(0, nwin - 1) * pl.n, np.nan)
+    rows = -(-pl.n // 4) * 4            # windows are padded to a multiple of 4 rows
+    ck = np.full(max(0, nwin - 1) * rows, np.nan)
     for (b, i), v in fw["colck"].items():
-        ck[(b - 1) * pl.n + i] = v
+        ck[(b - 1) * rows + i] = v
     return fr, ck
 
 
@@ -375,7 +391,7 @@ def kernel_backward(fw, pl, end):
         rf0 = RT * max(0, ps0)
         re0 = min(min(n, RT * min(nt, ps0 + KC)), wi + 1)
         ys = [ys_all[c0 + k] if c0 + k < M else 0.0 for k in range(KW)]
-        lcol = [ck[(b - 1) * n + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
+        lcol = [ck[(b - 1) * (-(-n // 4) * 4) + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
         frc = c * L * (W + E)
         fr_at = lambda j, th: fr[frc + ((j >> 2) * L + th) * 4 + (j & 3)]             # noqa: E731
         rec_at = lambda e, th: fr[frc + (((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]  # noqa: E731
@@ -387,46 +403,65 @@ def kernel_backward(fw, pl, end):
                       rf_left=RT * max(0, ps + 1), e=[0.0] * 4, dd=0.0)
             tau = tau0 + d
             if 1 <= ps <= nt:
-                st["D"] = [fr_at(sub * WB + k, tau) for k in range(WB)]
-                st["B"] = rec_at(2 if RT == 2 else 4, tau)
-                st["dg"] = rec_at(RT - 1, tau) if sub == 0 else fr_at(sub * WB - 1, tau)
+                Bn, dl = rebase(rec_at(2 if RT == 2 else 4, tau), fr_at(0, tau))
+                st["D"] = [r32(fr_at(sub * WB + k, tau) - dl) for k in range(WB)]
+                st["B"] = Bn
+                st["dg"] = r32((rec_at(RT - 1, tau) if sub == 0 else fr_at(sub * WB - 1, tau)) - dl)
             else:
                 st["D"], st["B"], st["dg"] = [0.0] * WB, 0.0, 0.0
             if sub == 0 and d >= 1:
                 bsrc = 0.0
                 if 1 <= ps + 1 <= nt:
+                    bsrc, dl = rebase(rec_at(2 if RT == 2 else 4, tau - 1), fr_at(0, tau - 1))
                     if RT == 2:
-                        st["e"] = [rec_at(0, tau - 1), fr_at(W - 1, tau - 1), 0.0, 0.0]
+                        e = [rec_at(0, tau - 1), fr_at(W - 1, tau - 1), 0.0, 0.0]
                     else:
-                        st["e"] = [rec_at(0, tau - 1), rec_at(1, tau - 1), rec_at(2, tau - 1), fr_at(W - 1, tau - 1)]
-                    bsrc = rec_at(2 if RT == 2 else 4, tau - 1)
+                        e = [rec_at(0, tau - 1), rec_at(1, tau - 1), rec_at(2, tau - 1), fr_at(W - 1, tau - 1)]
+                    st["e"] = [r32(v - dl) for v in e]
                 st["dd"] = r32(bsrc - st["B"])
             st["y"] = ys[lane * WB:(lane + 1) * WB]
             lanes.append(st)
-        steps = wi - rtop + 32
+        # lane l handles rows r, r+1 (r - rtop even) at step (r - rtop) / 2 + l
+        steps = (wi - rtop) // 2 + 32
         dirs = {}
+        for st in lanes:
+            st["last"] = [0.0, 0.0]
         for sg in range(steps):
-            recv = [lanes[max(0, lane - 1)]["D"][WB - 1] for lane in range(32)]
+            recv = [lanes[max(0, lane - 1)]["last"][:] for lane in range(32)]
             for lane, st in enumerate(lanes):
-                r = sg + rtop - lane
-                if not (st["rf"] <= r < st["re"] and r <= wi):
+                r = rtop + 2 * (sg - lane)
+                hi = min(st["re"], wi + 1)
+                if not (st["rf"] <= r < hi):
                     continue
-                if st["sub"] != 0:
-                    left = recv[lane]
-                elif st["d"] == 0:
-                    left = INF if b == 0 else lcol[r - rf0]
-                else:
-                    v = recv[lane] if r >= st["rf_left"] else st["e"][r - RT * st["ps"]]
-                    left = r32(v + st["dd"])
-                conv, code, dg = left, [], st["dg"]
+                vb = r + 1 < hi
+                lefts = []
+                for h in range(2):
+                    rr = r + h
+                    if h == 1 and not vb:
+                        lefts.append(INF)
+                    elif st["sub"] != 0:
+                        lefts.append(recv[lane][h])
+                    elif st["d"] == 0:
+                        lefts.append(INF if b == 0 else lcol[rr - rf0])
+                    else:
+                        v = recv[lane][h] if r >= st["rf_left"] else st["e"][rr - RT * st["ps"]]
+                        lefts.append(r32(v + st["dd"]))
+                lA, lB = lefts
+                dgA, dgB = st["dg"], lA
+                cA, cB = [], []
                 for k in range(WB):
                     up = st["D"][k]
-                    nv, cc = cell(xs[r], st["y"][k], up, dg, left)
-                    code.append(cc)
-                    dg, left = up, nv
-                    st["D"][k] = nv
-                st["dg"] = conv
-                dirs[(sg, lane)] = code
+                    nA, ca = cell(xs[r], st["y"][k], up, dgA, lA)
+                    dgA, lA = up, nA
+                    nB, cb = cell(xs[r + 1], st["y"][k], nA, dgB, lB)
+                    dgB, lB = nA, nB
+                    cA.append(ca)
+                    cB.append(cb)
+                    st["D"][k] = nB if vb else nA
+                st["last"] = [dgB, lB]           # row r's and row r+1's last column
+                st["dg"] = lefts[1] if vb else lefts[0]
+                dirs[(2 * sg, lane)] = cA
+                dirs[(2 * sg + 1, lane)] = cB
         if first:
             lj, kj = (wj - c0) // WB, (wj - c0) % WB
             v_end = r32(lanes[lj]["D"][kj] + lanes[lj]["B"])
@@ -444,7 +479,7 @@ def kernel_backward(fw, pl, end):
                     cc = jk - c0
                     lam = cc // WB
                     if wi >= RT * max(0, ps0 - (lam >> 2)):
-                        code = UP if jk == 0 else dirs[(wi - rtop + lam, lam)][cc - lam * WB]
+                        code = UP if jk == 0 else dirs[(wi - rtop + 2 * lam, lam)][cc - lam * WB]
                 codes.append(code)
             f = next((k for k in range(32) if codes[k] != LEFT), 32)
             fcode = codes[f] if f < 32 else LEFT

@@ -173,13 +173,13 @@ def test_backward_ragged(gpu):
 def _ckpt_floats_per_query(M, N, W, P, RT):
     """Backward workspace per query (floats) of a checkpointing plan: the
     wavefront slot (one record of W + 4 or W + 8 floats per thread and chunk of
-    32 steps), the boundary columns every 8 W columns, a gradient row and 7
+    32 steps), the boundary columns every 8 W columns (rows padded to 4), a gradient row and 7
     scalars (the layout the library documents)."""
     S, lag_last = 32 * P * W, (P - 1) * 64 + 31
     nsw, nt = -(-M // S), -(-N // RT)
     total = (nsw - 1) * max(nt, lag_last + 32) + nt + lag_last
     fr = -(-total // 32) * 32 * P * (W + (4 if RT == 2 else 8))
-    ck = (-(-M // (8 * W)) - 1) * N
+    ck = (-(-M // (8 * W)) - 1) * (-(-N // 4) * 4)
     return fr + ck + M + 7
 
 
