@@ -83,8 +83,6 @@ typedef struct sdtw_config {
     uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
     uint32_t flags;              /* SDTW_FLAG_* */
     int32_t tile_rows;           /* query rows a thread advances per step (2 or 4); 0 = chosen by the library */
-    int32_t ctas_per_query;      /* CTAs sharing one query's chain (1, or 2 as a thread-block cluster; needs an
-                                    even warps_per_query; uniform batches only); 0 = chosen by the library */
 } sdtw_config;
 
 /* Description of how a call of a given shape will run (for reports and tests). */

@@ -49,7 +49,6 @@ class sdtw_config(ctypes.Structure):
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),
         ("tile_rows", ctypes.c_int32),
-        ("ctas_per_query", ctypes.c_int32),
     ]
 
 

@@ -65,8 +65,6 @@ struct CkptKey {
 struct sdtw_ctx {
     sdtw_config cfg{};
     int sm_count = 0;
-    int smem_per_sm = 0;        // shared memory of one SM (bytes)
-    int smem_reserved = 0;      // shared memory the system reserves per CTA
     std::string err;
     size_t cap = kDefaultCap;
     size_t ws_bytes = 0;
@@ -86,7 +84,7 @@ struct sdtw_ctx {
     // host-call staging
     DevBuf st_ref, st_q, st_off, st_cost, st_end, st_gc, st_gq, st_gr, st_path;
 
-    std::map<TuneKey, std::tuple<int, int, int, int>> tuned;  // -> (W, P, RT, CL)
+    std::map<TuneKey, std::tuple<int, int, int>> tuned;  // -> (W, P, RT)
 };
 
 namespace {
@@ -134,68 +132,33 @@ sdtw_status ensure(sdtw_ctx* c, DevBuf& b, size_t bytes)
     return s;
 }
 
-// Grid, block and shared memory of a plan.  With CL > 1 (a query's chain split
-// over a cluster of CL CTAs) the dynamic shared memory is padded so that no SM
-// holds more than ceil(CL B / SMs) CTAs: the batch then spreads evenly over
-// the SMs instead of leaving some with one query more than others; if the
-// clusters do not all fit at once the plan falls back to one CTA per query.
-void set_launch(const sdtw_ctx* c, FwdPlan& p, int B, int N, bool ckpt)
-{
-    const sdtw_dtype dt = c->cfg.dtype;
-    if (p.persistent || p.P % 2 != 0) p.CL = 1;
-    for (;;) {
-        p.block = 32 * p.P / p.CL;
-        p.smem = sdtw::fwd_smem_bytes(dt, N, p.P, p.W, p.RT, p.CL);
-        if (p.persistent) {
-            const int per_sm = sdtw::fwd_max_ctas_per_sm(dt, p.W, p.P, p.smem, p.RT, ckpt);
-            p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
-            return;
-        }
-        if (p.CL == 1) {
-            p.grid = B;
-            return;
-        }
-        const int target = static_cast<int>((static_cast<int64_t>(p.CL) * B + c->sm_count - 1) / c->sm_count);
-        const int natural = sdtw::fwd_max_ctas_per_sm(dt, p.W, p.P / p.CL, p.smem, p.RT, ckpt);
-        if (natural > target && target > 0 && c->smem_per_sm > 0) {
-            // (the kernel's own static shared memory counts against the
-            // per-CTA limit too: keep 1 KiB below it)
-            int pad = (c->smem_per_sm / target - c->smem_reserved) / 16 * 16;
-            pad = std::min(pad, kMaxSmem - 1024);
-            if (pad > p.smem && sdtw::fwd_max_ctas_per_sm(dt, p.W, p.P / p.CL, pad, p.RT, ckpt) <= target &&
-                sdtw::fwd_max_ctas_per_sm(dt, p.W, p.P / p.CL, pad, p.RT, ckpt) > 0)
-                p.smem = pad;
-        }
-        p.grid = p.CL * B;
-        if (sdtw::fwd_max_clusters(dt, p.W, p.P, p.smem, p.RT, ckpt, p.CL) >= B) return;
-        p.CL = 1;  // the clusters would run in more than one wave
-    }
-}
-
 // default plan for a forward call
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
     // defaults measured on the paper's batch: 24 columns x 4 rows per thread,
-    // four warps per query, one CTA per query (splitting the chain over a
-    // two-CTA cluster spreads the 512 queries more evenly over the SMs but
-    // measured slower: 22.4 ms against 20.0 ms; the autotuner times both)
+    // four warps per query
     FwdPlan p;
     p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : 24;
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
     p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
-    p.CL = c->cfg.ctas_per_query > 0 ? c->cfg.ctas_per_query : 1;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
         if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
         if (c->cfg.warps_per_query <= 0) p.P = std::get<1>(it->second);
         if (c->cfg.tile_rows <= 0) p.RT = std::get<2>(it->second);
-        if (c->cfg.ctas_per_query <= 0) p.CL = std::get<3>(it->second);
     }
     // a short reference needs fewer threads per query (unless the caller fixed P)
     if (c->cfg.warps_per_query <= 0)
         while (p.P > 1 && static_cast<int64_t>(32) * (p.P / 2) * p.W >= M) p.P /= 2;
+    p.block = 32 * p.P;
+    p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, p.RT);
     p.persistent = ragged;
-    set_launch(c, p, B, N, ckpt);
+    if (p.persistent) {
+        int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
+        p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
+    } else {
+        p.grid = B;
+    }
     return p;
 }
 
@@ -276,7 +239,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     if (p.smem > kMaxSmem) return SDTW_E_UNSUPPORTED;
     if (sdtw::fwd_total_steps(M, N, p.W, p.P, p.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (p.persistent) p.grid = std::min(p.grid, nq);
-    else p.grid = p.CL * nq;
+    else p.grid = nq;
     FwdArgs a{};
     a.ref = ref;
     a.M = M;
@@ -413,7 +376,6 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
-    if (cfg->ctas_per_query < 0 || cfg->ctas_per_query > 2) return SDTW_E_INVALID;
     if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0) return SDTW_E_INVALID;
     if (cfg->ckpt_stride != 0 && cfg->ckpt_stride != sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
@@ -425,10 +387,6 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     c->cap = cfg->mem_cap_bytes ? cfg->mem_cap_bytes : kDefaultCap;
     cudaError_t e = cudaSetDevice(cfg->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, cfg->device);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&c->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, cfg->device);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -675,28 +633,27 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
     float best_ms = 1e30f;
-    int best_w = 0, best_p = 0, best_rt = 0, best_cl = 1;
+    int best_w = 0, best_p = 0, best_rt = 0;
     const int Ws[] = {8, 16, 24, 32};
-    const int Ps[] = {1, 2, 3, 4, 6, 8, 16};
+    const int Ps[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
     const int RTs[] = {2, 4};
     for (int RT : RTs) {
         for (int W : Ws) {
             for (int P : Ps) {
-                for (int CL = 1; CL <= 2; ++CL) {
                 if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
-                if (CL > 1 && (ragged || P % CL != 0)) continue;
                 FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
                 p.W = W;
                 p.P = P;
                 p.RT = RT;
-                p.CL = CL;
-                set_launch(ctx, p, B, N, ckpt);
-                if (p.CL != CL) continue;  // the clusters would not fit at once
+                p.block = 32 * P;
+                p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, RT);
                 if (p.smem > kMaxSmem) continue;
                 const CkLayout l = ck_layout(M, N, p);
                 if (ckpt && B > chunk_capacity(ctx, l)) continue;
                 const CkPtrs ck = ckpt ? carve(ctx, l, B, M) : CkPtrs{};
-                if (sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P / CL, p.smem, RT, ckpt) <= 0) continue;
+                const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
+                if (per_sm <= 0) continue;
+                p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : B;
                 // one untimed run, then the best of two timed runs
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
@@ -727,8 +684,6 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                     best_w = W;
                     best_p = P;
                     best_rt = RT;
-                    best_cl = CL;
-                }
                 }
             }
         }
@@ -737,7 +692,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     cudaEventDestroy(e1);
     if (best_w == 0) return SDTW_E_UNSUPPORTED;
     ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] =
-        std::make_tuple(best_w, best_p, best_rt, best_cl);
+        std::make_tuple(best_w, best_p, best_rt);
     ctx->key.valid = false;
     if (plan) return sdtw_get_plan(ctx, B, N, M, ragged ? 1 : 0, 0, plan);
     return SDTW_OK;
@@ -753,7 +708,7 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
     std::memset(plan, 0, sizeof(*plan));
     plan->seg_width = p.W;
     plan->warps_per_query = p.P;
-    plan->ctas_per_query = p.CL;
+    plan->ctas_per_query = 1;
     plan->persistent = p.persistent ? 1 : 0;
     plan->grid = p.persistent ? p.grid : B;
     plan->block = p.block;

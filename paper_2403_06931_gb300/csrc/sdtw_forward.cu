@@ -57,7 +57,6 @@
 // left inputs it uses, already converted into its own base.  From a chunk's
 // wavefront and those columns the backward recomputes any K-column window of
 // the chunk with the forward's own operations, bit for bit.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -191,40 +190,23 @@ fwd_chain_kernel(const FwdArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_query;
 
-    // The chain of one query may span the CL CTAs of a thread-block cluster
-    // (CL = 1 without a cluster launch): thread tid of the chain is thread
-    // threadIdx.x of the CTA of rank tid / blockDim.x.
-    namespace cg = cooperative_groups;
-    const int CL = static_cast<int>(cg::this_cluster().num_blocks());
-    const int rank = static_cast<int>(cg::this_cluster().block_rank());
-    const int Pc = blockDim.x >> 5;  // warps in this CTA
-    const int P = Pc * CL;           // warps in the chain
-    const int L = P * 32;            // threads in the chain
-    const int tid = rank * blockDim.x + threadIdx.x;
-    const int warp = tid >> 5;
+    const int P = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int N = a.N;
     const int Npad = (N + RT - 1) / RT * RT;
     const int M = static_cast<int>(a.M);
-    const int S = L * W;
+    const int S = blockDim.x * W;
     const int nsw = (M + S - 1) / S;
-    // barrier of the whole chain: its CTA, or its cluster
-    auto chain_sync = [&]() {
-        if (CL > 1)
-            cg::this_cluster().sync();
-        else
-            __syncthreads();
-    };
 
-    // shared memory of each CTA: the input rings of its warps [Pc][kRing] and
-    // the column buffer [Npad/RT] of edges (rank 0's is used); query samples
-    // [Npad] (zero padded); reduction scratch (value, index) for its warps and
-    // for the cluster's CTAs.  Every part is 16-byte aligned.
+    // shared memory: ring [P][kRing] and column buffer [Npad/RT] of edges;
+    // query samples [Npad] (zero padded); reduction scratch (value, index)[P].
+    // Every part is 16-byte aligned.
     E* ring = reinterpret_cast<E*>(smem_raw);
-    E* colbuf = ring + Pc * kRing;
+    E* colbuf = ring + P * kRing;
     V* xs = reinterpret_cast<V*>(colbuf + Npad / RT);  // [Npad]
-    V* red_v = xs + Npad;                              // [Pc + CL]
-    int* red_i = reinterpret_cast<int*>(red_v + Pc + CL);  // [Pc + CL]
+    V* red_v = xs + Npad;                              // [P]
+    int* red_i = reinterpret_cast<int*>(red_v + P);    // [P]
 
     const Tin* ref = static_cast<const Tin*>(a.ref);
     const Tin* queries = static_cast<const Tin*>(a.queries);
@@ -232,38 +214,23 @@ fwd_chain_kernel(const FwdArgs a)
     const int wlag = warp * (32 + kChunk);
     const int lag = wlag + lane;
     const int lag_last = (P - 1) * (32 + kChunk) + 31;
-    const E* ring_in = ring + (warp - rank * Pc) * kRing;
-    // the next warp's input ring, in this CTA or (for the CTA's last warp) in
-    // the next CTA of the cluster; the chain's last thread writes the column
-    // buffer of rank 0.  Only lane 31 writes through these, and only stores
-    // cross CTAs: every load is from the CTA's own shared memory.
-    E* ring_out = nullptr;
-    E* colbuf_out = colbuf;
-    if (CL > 1) {
-        if (warp + 1 < P)
-            ring_out = (warp + 1) / Pc == rank ? ring + (warp + 1 - rank * Pc) * kRing
-                                               : cg::this_cluster().map_shared_rank(ring, rank + 1);
-        colbuf_out = cg::this_cluster().map_shared_rank(colbuf, 0);
-    } else {
-        ring_out = ring + (warp + 1) * kRing;
-    }
+    const E* ring_in = ring + warp * kRing;
+    E* ring_out = ring + (warp + 1) * kRing;
     const V INF = Md::inf();
     constexpr int EREC = fwd_record_floats(RT);  // floats of a thread's checkpoint record
+    const int L = blockDim.x;
 
     for (int it = 0;; ++it) {
         int q;
         if (a.queue) {
-            if (tid == 0) {
-                const int v = atomicAdd(a.queue, 1);
-                for (int r = 0; r < CL; ++r) *cg::this_cluster().map_shared_rank(&s_query, r) = v;
-            }
-            chain_sync();
+            if (threadIdx.x == 0) s_query = atomicAdd(a.queue, 1);
+            __syncthreads();
             q = s_query;
             if (q >= a.B) break;
             q = a.order ? a.order[q] : a.q0 + q;
         } else {
             if (it > 0) break;
-            q = a.q0 + static_cast<int>(blockIdx.x) / CL;
+            q = a.q0 + blockIdx.x;
         }
 
         int64_t start;
@@ -275,8 +242,8 @@ fwd_chain_kernel(const FwdArgs a)
             const int64_t len = stop - start;
             bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total];
             if (bad) {
-                if (tid == 0) atomicOr(a.status, kStatusBadLength);
-                chain_sync();
+                if (threadIdx.x == 0) atomicOr(a.status, kStatusBadLength);
+                __syncthreads();
                 continue;
             }
             n = static_cast<int>(len);
@@ -285,18 +252,18 @@ fwd_chain_kernel(const FwdArgs a)
             n = N;
         }
         if (n == 0) {
-            if (tid == 0) {
+            if (threadIdx.x == 0) {
                 static_cast<V*>(a.cost)[q] = Md::empty_cost();
                 a.end[q] = -1;
             }
-            chain_sync();
+            __syncthreads();
             continue;
         }
 
         const int nt = (n + RT - 1) / RT;  // tiles of rows per sweep
         for (int i = threadIdx.x; i < nt * RT; i += blockDim.x)
             xs[i] = i < n ? Md::widen(queries[start + i]) : Md::zero();  // dummy rows complete the last tile
-        chain_sync();
+        __syncthreads();
 
         const int lastt = nt - 1;                 // the tile holding row n-1
         const int bot = (n - 1) - RT * lastt;     // ... as its row bot
@@ -317,7 +284,7 @@ fwd_chain_kernel(const FwdArgs a)
         int best_col = INT_MAX;
         int p = -lag;   // tile of this thread's strip in sweep s (negative: not started)
         int s = 0;      // sweep
-        int base = tid * W;  // first column of the strip in sweep s
+        int base = threadIdx.x * W;  // first column of the strip in sweep s
         // checkpoints of this query: the wavefront slot and, for a strip that
         // starts at a multiple of K, its boundary column
         float* frq = CKPT ? a.fr + static_cast<int64_t>(q - a.q0) * a.fr_slot : nullptr;
@@ -392,7 +359,7 @@ fwd_chain_kernel(const FwdArgs a)
                         if (warp < P - 1)
                             ring_out[t & (kRing - 1)] = e;
                         else
-                            colbuf_out[p] = e;
+                            colbuf[p] = e;
                     }
                     if constexpr (CKPT) {
                         if (ck) store_rows<RT>(ck + RT * p, left);
@@ -434,7 +401,7 @@ fwd_chain_kernel(const FwdArgs a)
                         if (p == 0) {
                             // new sweep: load the strip's reference samples; the
                             // previous row is the virtual all-zero row -1
-                            base = s * S + tid * W;
+                            base = s * S + threadIdx.x * W;
 #pragma unroll
                             for (int k = 0; k < W; ++k) {
                                 const int col = base + k;
@@ -471,7 +438,7 @@ fwd_chain_kernel(const FwdArgs a)
                             if (warp < P - 1)
                                 ring_out[t & (kRing - 1)] = e;
                             else
-                                colbuf_out[p] = e;
+                                colbuf[p] = e;
                         }
                         if constexpr (CKPT) {
                             if (ck) store_rows<RT>(ck + RT * p, left);  // padding rows fall in the padded slot
@@ -491,7 +458,8 @@ fwd_chain_kernel(const FwdArgs a)
                 // previous sweep's last tile when the period has no idle steps)
                 const int c1 = t0 / kChunk + 1;
                 if (t0 + kChunk < total && ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt))) {
-                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(c1) * L * (W + EREC)) + tid;
+                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(c1) * L * (W + EREC)) +
+                                 threadIdx.x;
 #pragma unroll
                     for (int k = 0; k < W / 4; ++k)
                         __stcs(f4 + k * L, make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]));
@@ -503,10 +471,10 @@ fwd_chain_kernel(const FwdArgs a)
                     }
                 }
             }
-            chain_sync();
+            __syncthreads();
         }
 
-        // lexicographic (value, column) minimum over the chain
+        // lexicographic (value, column) minimum over the CTA
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const V ov = __shfl_down_sync(0xffffffffu, best, off);
@@ -517,37 +485,17 @@ fwd_chain_kernel(const FwdArgs a)
             }
         }
         if (lane == 0) {
-            red_v[warp - rank * Pc] = best;
-            red_i[warp - rank * Pc] = best_col;
+            red_v[warp] = best;
+            red_i[warp] = best_col;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             V bv = red_v[0];
             int bc = red_i[0];
-            for (int w = 1; w < Pc; ++w) {
+            for (int w = 1; w < P; ++w) {
                 if (red_v[w] < bv || (red_v[w] == bv && red_i[w] < bc)) {
                     bv = red_v[w];
                     bc = red_i[w];
-                }
-            }
-            // this CTA's minimum into slot Pc + rank of rank 0
-            V* cv = red_v + Pc + rank;
-            int* ci = red_i + Pc + rank;
-            if (CL > 1) {
-                cv = cg::this_cluster().map_shared_rank(cv, 0);
-                ci = cg::this_cluster().map_shared_rank(ci, 0);
-            }
-            *cv = bv;
-            *ci = bc;
-        }
-        chain_sync();
-        if (tid == 0) {
-            V bv = red_v[Pc];
-            int bc = red_i[Pc];
-            for (int r = 1; r < CL; ++r) {
-                if (red_v[Pc + r] < bv || (red_v[Pc + r] == bv && red_i[Pc + r] < bc)) {
-                    bv = red_v[Pc + r];
-                    bc = red_i[Pc + r];
                 }
             }
             static_cast<V*>(a.cost)[q] = bv;
@@ -557,7 +505,7 @@ fwd_chain_kernel(const FwdArgs a)
                 a.ck_end[q - a.q0] = bc;
             }
         }
-        chain_sync();  // the reduction slots are reused by the next query
+        __syncthreads();
     }
 }
 
@@ -585,50 +533,15 @@ struct Inst {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
             if (e != cudaSuccess) return e;
         }
-        if (plan.CL <= 1) {
-            k<<<plan.grid, plan.block, plan.smem, s>>>(a);
-            return cudaGetLastError();
-        }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3(plan.grid, 1, 1);
-        cfg.blockDim = dim3(plan.block, 1, 1);
-        cfg.dynamicSmemBytes = plan.smem;
-        cfg.stream = s;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = plan.CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k, a);
+        k<<<plan.grid, plan.block, plan.smem, s>>>(a);
+        return cudaGetLastError();
     }
-    // CTAs of `block` threads and `smem` bytes resident per SM (CL = 1), or
-    // clusters of CL such CTAs resident on the whole GPU (CL > 1)
-    static int occupancy(int block, int smem, int CL)
+    static int occupancy(int block, int smem)
     {
         int n = 0;
         auto k = fwd_chain_kernel<Tin, W, RT, CKPT>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (CL <= 1) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
-            return n;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3(CL, 1, 1);
-        cfg.blockDim = dim3(block, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
         return n;
     }
 };
@@ -662,16 +575,16 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 
 bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
 
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT, int CL)
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT)
 {
-    // per CTA: the rings of its P/CL warps [kRing] and the column buffer
-    // [Npad/RT] of edges (16 bytes for RT = 2, 32 for RT = 4), query samples
-    // [Npad] and the reduction (value, index)[P/CL + CL], 4-byte elements
+    // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
+    // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
+    // 4-byte elements
     (void)dt;
     (void)W;
     const int npad = (N + RT - 1) / RT * RT;
     const int esz = RT == 2 ? 16 : 32;
-    return esz * ((P / CL) * kRing + npad / RT) + 4 * (npad + 2 * (P / CL + CL));
+    return esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
@@ -706,17 +619,7 @@ int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt
 {
     int n = 0;
     dispatch(dt, W, RT, ckpt, [&](auto inst) {
-        n = decltype(inst)::occupancy(32 * P, smem, 1);
-        return cudaSuccess;
-    });
-    return n;
-}
-
-int fwd_max_clusters(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt, int CL)
-{
-    int n = 0;
-    dispatch(dt, W, RT, ckpt, [&](auto inst) {
-        n = decltype(inst)::occupancy(32 * P / CL, smem, CL);
+        n = decltype(inst)::occupancy(32 * P, smem);
         return cudaSuccess;
     });
     return n;

@@ -70,18 +70,16 @@ struct FwdPlan {
     int W = 16;          // segment width: reference columns per thread
     int P = 8;           // warps per query chain
     int RT = 2;          // query rows per thread per step (tile height)
-    int CL = 1;          // CTAs per query chain (a thread-block cluster when > 1)
     bool persistent = false;
-    int grid = 0;        // CTAs launched
-    int block = 0;       // threads per CTA (32 P / CL)
-    int smem = 0;        // dynamic shared memory per CTA
+    int grid = 0;
+    int block = 0;
+    int smem = 0;
 };
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT, int CL);
+int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT);
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt);
-int fwd_max_clusters(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt, int CL);
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s);

@@ -71,7 +71,7 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     plan.RT = 4;
     while (plan.P > 1 && static_cast<int64_t>(32) * (plan.P / 2) * plan.W >= M) plan.P /= 2;
     plan.block = 32 * plan.P;
-    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, plan.RT, 1);
+    plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, plan.RT);
     plan.persistent = true;
     if (plan.smem > 227 * 1024) return SDTW_E_UNSUPPORTED;
     if (sdtw::fwd_total_steps(M, N, plan.W, plan.P, plan.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;

@@ -29,7 +29,6 @@ def main():
     ap.add_argument("--seg-width", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--ctas", type=int, default=0, help="CTAs per query chain (1, or 2 as a cluster)")
     ap.add_argument("--keep-checkpoints", action="store_true",
                     help="the forward stores backward checkpoints (implied by --backward)")
     a = ap.parse_args()
@@ -50,8 +49,7 @@ def main():
     ctx = SdtwContext(dtype=a.dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=N,
                       max_total_query_len=qs.numel(), grad=a.backward or a.keep_checkpoints,
                       keep_checkpoints=a.backward or a.keep_checkpoints,
-                      seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows,
-                      ctas_per_query=a.ctas)
+                      seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows)
     if a.autotune:
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None

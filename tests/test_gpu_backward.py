@@ -153,19 +153,6 @@ def test_backward_every_tile_height_and_width(gpu, RT, W):
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
 
-@pytest.mark.parametrize("W,RT", [(24, 4), (32, 2)])
-def test_backward_after_cluster_split_forward(gpu, W, RT):
-    # checkpoints written by a chain split over a two-CTA cluster are the
-    # one-CTA chain's: the backward's results are identical
-    w = inputs.tiny(B=3, N=700, M=9000, seed=410 + W)
-    a = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=4, ctas_per_query=1)
-    b = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=4, ctas_per_query=2)
-    for k in range(5):
-        assert np.array_equal(a[k], b[k])
-    oc, _ = oracle.forward_batch(w.ref, w.queries)
-    check_validity(w, *b, range(w.B), oc)
-
-
 def test_backward_long_vertical_runs_cross_bands(gpu):
     # a query far longer than the reference forces long vertical runs, so the
     # walk climbs through many bands of one window

@@ -85,24 +85,6 @@ def test_fast_path_plans(gpu, W, P, RT):
         assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
 
 
-@pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 24, 32])
-@pytest.mark.parametrize("P", [2, 4, 8])
-def test_cluster_split_is_bit_identical(gpu, W, P, RT):
-    # a chain split over a two-CTA cluster runs the same arithmetic: results
-    # equal the one-CTA chain's bit for bit (and the oracle's within tolerance)
-    for (B, N, M) in ((3, 91, 6000), (2, 1203, 20000), (4, 7, 333)):
-        w = inputs.tiny(B=B, N=N, M=M, seed=90 + N + M)
-        c1, e1 = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT, ctas_per_query=1)
-        c2, e2 = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT, ctas_per_query=2)
-        assert np.array_equal(c1, c2) and np.array_equal(e1, e2)
-        assert parity.check_forward_f32(w.ref, w.query, range(w.B), c2, e2) == []
-    wi = inputs.paper_i8(B=3, N=501, M=9000, seed=91)
-    c2, e2 = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT,
-                     ctas_per_query=2)
-    assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), c2, e2) == []
-
-
 def test_exact_cut_has_zero_cost(gpu):
     w = inputs.tiny(B=1, N=10, M=3000, seed=5)
     y = w.ref
