@@ -37,10 +37,13 @@ OPS_PER_CELL = 6          # instruction-issue roofline: ops per DP cell (subtrac
 LANES_PER_SM = 128        # 4 schedulers x 32 lanes
 L2_FLUSH_BYTES = 512 << 20
 
-# ncu DRAM traffic of one forward launch on the paper batch, valid only while
-# the forward kernel source hashes to FWD_SRC_SHA (else reported as null)
-FWD_SRC_SHA = None
-FWD_TRAFFIC_BYTES = None
+# ncu DRAM traffic of one checkpointing forward launch on the paper batch, valid
+# only while the forward kernel source hashes to FWD_SRC_SHA (else reported as
+# null).  Captured on 128 of the 512 queries (2,341,632 bytes read + 1,553,270,784
+# written: the writes are the per-query checkpoints) and scaled by 4 to the
+# 512-query launch; profiles/fwd_chain_kernel_f32_ckpt_W24_RT4_paper_512x2000_vs_100000.md
+FWD_SRC_SHA = "63783a939d396ea5"
+FWD_TRAFFIC_BYTES = 4 * (2_341_632 + 1_553_270_784)
 
 
 def src_sha(path):
@@ -315,6 +318,47 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
     ms = timed(lambda: ictx.forward(ri, qi, out=(ci, end)), 5)
     forms["forward_i8"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": iplan}
     ictx.close()
+
+    # batch z-normalisation (Section 5.1, Eq. 2) of the batch's 512 x 2,000 query
+    # samples, as the paper's Table 1 times it: HBM-bound, one read and one write
+    # per sample (the reference is done once per reference, one CTA)
+    from paper_2403_06931_gb300.sdtw import znormalize
+    zin = torch.from_numpy(inputs.random_walks(B, N, seed=11)).to(dev)
+    zout = torch.empty_like(zin)
+    znormalize(zin, out=zout)
+
+    def graph_ms(with_kernel, reps=20):
+        # a microsecond kernel timed alone would measure the host's launch gap:
+        # replay reps (flush, kernel) pairs from one CUDA graph and subtract the
+        # same graph without the kernel
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                flush.zero_()
+                if with_kernel:
+                    znormalize(zin, out=zout)
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms = max(graph_ms(True) - graph_ms(False), 1e-4)
+    zbytes = 8 * B * N
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs")
+    forms["znormalize"] = {"series": f"{B} x {N}", "ms": round(ms, 4), "gsps": round(B * N / (ms * 1e-3) / 1e9, 2),
+                           "gbs": round(zbytes / (ms * 1e-3) / 1e9, 1),
+                           "hbm_frac": round(zbytes / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                           "bytes": zbytes, "peak_basis": f"hbm_gbs, {pk_kind}",
+                           "note": "one read and one write per sample; L2 flushed before each run; kernel time = "
+                                   "20 (flush, kernel) pairs minus 20 flushes, each replayed from a CUDA graph"}
+    rin = torch.from_numpy(inputs.random_walks(1, M, seed=12).reshape(-1)).to(dev)
+    ms = timed(lambda: znormalize(rin, out=rin), 5)
+    forms["znormalize"]["reference_ms"] = round(ms, 4)
 
     if not args.no_ragged:
         wr = inputs.ragged_fp32()

@@ -185,6 +185,22 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
                           int32_t* path, void* stream);
 
 /*
+ * The warp path of every query without gradients (the paper's walk-back,
+ * Section 2, as in sdtw_backward): for row i of query q, path[2*(start_q+i)]
+ * and path[2*(start_q+i)+1] receive the first and last column of the path in
+ * that row (start_q = q*N or offsets[q]).
+ *   ref, queries, offsets, B, N, M, end: as in sdtw_backward.
+ *   path      device int32, 2 per query sample: overwritten.
+ * Needs an SDTW_F32 context with SDTW_FLAG_GRAD (it uses the checkpoint
+ * workspace); like sdtw_backward it reuses the checkpoints of a kept forward
+ * on the same inputs, else re-runs the forward with checkpoint stores.
+ * Errors: as sdtw_backward.
+ */
+sdtw_status sdtw_path(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries,
+                      const int64_t* offsets, int32_t B, int32_t N, const int64_t* end, int32_t* path,
+                      void* stream);
+
+/*
  * sdtw_forward from and to host memory (the paper's runSDTW shape: host batch
  * in, host results out).  Copies ref/queries/offsets into context-owned
  * device buffers, runs the forward, copies cost/end back and synchronises
@@ -225,6 +241,26 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
  * Errors: SDTW_E_INVALID. */
 sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_t ragged,
                           int32_t backward, sdtw_plan* plan);
+
+/*
+ * Batch z-normalisation (paper Section 5.1, Eq. 2): each series becomes
+ * (x - mean) / S with its own mean and population standard deviation S (the
+ * paper's code divides by n); a series with S == 0 is only centred.  The
+ * statistics are accumulated in double in two passes (the mean, then the
+ * centred second moment); the result is rounded once to float.  This is the
+ * standardisation the forward expects of its inputs (the library does not
+ * apply it implicitly).
+ *   in, out   device float: B series back to back, [B][N] or delimited by
+ *             offsets; out may equal in (in place).  Only the series' own
+ *             elements are written.
+ *   offsets   device int64 [B+1] (ascending) or NULL for B series of length N.
+ *             A series with offsets[q+1] <= offsets[q] is left untouched.
+ * No context and no allocation; asynchronous on `stream`.
+ * Errors: SDTW_E_INVALID (B < 0, N < 1 without offsets, null pointers with
+ * B > 0), SDTW_E_CUDA.
+ */
+sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N,
+                            void* stream);
 
 /* Largest batch sdtw_forward_noalloc accepts (its fixed device scratch holds
  * the query order for this many queries: 256 KiB per GPU). */

@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,7 +59,9 @@ def _load():
             lib.sdtw_oracle_forward_i64.argtypes = [_i, ctypes.c_int64, _i, ctypes.c_int64, _i, _i, _i]
             lib.sdtw_oracle_walkback_f64.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int64,
                                                      _i, _i, _i, _d]
-            for f in (lib.sdtw_oracle_forward_f64, lib.sdtw_oracle_forward_i64, lib.sdtw_oracle_walkback_f64):
+            lib.sdtw_oracle_znorm_f64.argtypes = [_d, ctypes.c_int64, _d]
+            for f in (lib.sdtw_oracle_forward_f64, lib.sdtw_oracle_forward_i64, lib.sdtw_oracle_walkback_f64,
+                      lib.sdtw_oracle_znorm_f64):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -99,6 +101,30 @@ def forward(x, y, last_row: bool = False):
     if rc != 0:
         raise ValueError(f"oracle forward failed (code {rc}) for n={np.size(x)}, m={np.size(y)}")
     return (c.value, e.value, row) if last_row else (c.value, e.value)
+
+
+def znormalize(x):
+    """Eq. 2 z-normalisation of one series in float64 (population statistics,
+    two passes; a series with zero spread is only centred)."""
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(xv)
+    st = _load().sdtw_oracle_znorm_f64(_p(xv, _d), len(xv), _p(out, _d))
+    if st != 0:
+        raise ValueError(f"oracle znorm failed ({st})")
+    return out
+
+
+def znormalize_batch(values, offsets=None, N=None):
+    """znormalize every series of a batch stored back to back ([B][N] or by offsets)."""
+    v = np.asarray(values, dtype=np.float64).reshape(-1)
+    out = np.empty_like(v)
+    if offsets is None:
+        bounds = [(i, i + N) for i in range(0, len(v), N)]
+    else:
+        bounds = [(int(offsets[q]), int(offsets[q + 1])) for q in range(len(offsets) - 1)]
+    for a, b in bounds:
+        out[a:b] = znormalize(v[a:b])
+    return out
 
 
 def default_threads() -> int:

@@ -24,9 +24,13 @@
  *            of that list.  In column 0 the only neighbour is (i-1,0); the path
  *            stops on reaching row 0.
  *
+ *   z-normalisation (Section 5.1, Eq. 2): the standardisation the paper
+ *            applies to the reference and every query before the fill.
+ *
  * Floating point is double throughout; the integer variant uses int64 and is
  * exact.  Everything is a straightforward row-by-row scalar loop.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -219,5 +223,32 @@ int sdtw_oracle_walkback_f64(const double* x, int64_t n, const double* y, int64_
 #undef AT
     *path_len = L;
     free(D);
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------ z-norm -- */
+
+/*
+ * Eq. 2 (paper Section 5.1): z = (x - mean) / S, with the series' own mean
+ * and standard deviation.  The paper's text says "sample" statistics but its
+ * code divides by n; the population form (divide by n) is taken.  Two passes
+ * in double: the mean, then the centred second moment.  A series with S == 0
+ * (constant, or of length 1) is only centred.  out may equal x.
+ */
+int sdtw_oracle_znorm_f64(const double* x, int64_t n, double* out)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) return ORACLE_EINVAL;
+    if (n == 0) return ORACLE_OK;
+    double sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) sum += x[i];
+    const double mean = sum / (double)n;
+    double ss = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double c = x[i] - mean;
+        ss += c * c;
+    }
+    double s = sqrt(ss / (double)n);
+    if (!(s > 0.0)) s = 1.0;
+    for (int64_t i = 0; i < n; ++i) out[i] = (x[i] - mean) / s;
     return ORACLE_OK;
 }

@@ -86,11 +86,13 @@ SIGNATURES = [
     ("sdtw_destroy", _ST, [_P]),
     ("sdtw_forward", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
     ("sdtw_backward", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P]),
+    ("sdtw_path", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
     ("sdtw_forward_host", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
     ("sdtw_forward_backward_host", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("sdtw_autotune", _ST, [_P, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P, ctypes.POINTER(sdtw_plan)]),
     ("sdtw_get_plan", _ST, [_P, _I32, _I32, _I64, _I32, _I32, ctypes.POINTER(sdtw_plan)]),
     ("sdtw_forward_noalloc", _ST, [ctypes.c_int, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
+    ("sdtw_znormalize", _ST, [_P, _P, _P, _I32, _I32, _P]),
     ("sdtw_last_device_status", _ST, [_P, _P]),
     ("sdtw_last_error", ctypes.c_char_p, [_P]),
     ("sdtw_workspace_bytes", ctypes.c_size_t, [_P]),
@@ -169,6 +171,10 @@ def sdtw_backward(ctx, ref, M, queries, offsets, B, N, end, grad_cost, grad_quer
                                 path, stream)
 
 
+def sdtw_path(ctx, ref, M, queries, offsets, B, N, end, path, stream) -> int:
+    return load().sdtw_path(ctx, ref, M, queries, offsets, B, N, end, path, stream)
+
+
 def sdtw_forward_host(ctx, ref, M, queries, offsets, B, N, cost, end, stream) -> int:
     return load().sdtw_forward_host(ctx, ref, M, queries, offsets, B, N, cost, end, stream)
 
@@ -197,6 +203,10 @@ def sdtw_forward_noalloc(dtype, ref, M, queries, offsets, B, N, cost, end, strea
 
 
 SDTW_NOALLOC_MAX_BATCH = 65536
+
+
+def sdtw_znormalize(inp, out, offsets, B, N, stream) -> int:
+    return load().sdtw_znormalize(inp, out, offsets, B, N, stream)
 
 
 def sdtw_last_device_status(ctx, stream) -> int:

@@ -450,24 +450,14 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
     return run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, nullptr, 0, B);
 }
 
-sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
-                          int32_t B, int32_t N, const int64_t* end, const float* grad_cost, float* grad_queries,
-                          float* grad_ref, int32_t* path, void* stream)
+// The walk-back of every query from its end column, chunk by chunk of
+// queries; with grad_queries == nullptr only the path is written.
+static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
+                         int32_t B, int32_t N, const int64_t* end, const float* grad_cost, float* grad_queries,
+                         float* grad_ref, int32_t* path, cudaStream_t st)
 {
-    if (!ctx) return SDTW_E_INVALID;
-    if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
-    if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
-    sdtw_status s = check_common(ctx, ref, M, queries, B, N, end, grad_cost);
-    if (s != SDTW_OK) return s;
-    if (B > 0 && (!grad_queries || !grad_ref)) return SDTW_E_INVALID;
-    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sdtw_status s;
     cudaError_t e;
-    if (B == 0) {
-        if (!grad_ref) return SDTW_E_INVALID;
-        if ((e = cudaMemsetAsync(grad_ref, 0, 4 * static_cast<size_t>(M), st)) != cudaSuccess) return cuda_fail(ctx, e);
-        return SDTW_OK;
-    }
     // the plan of the checkpoints: the kept forward's, or the one re-run here
     const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N);
     FwdPlan p = ckpt_plan(ctx, B, N, M, offsets != nullptr);
@@ -516,11 +506,46 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
         a.span = ck.span;
         a.status = ctx->d_status;
         if ((e = sdtw::launch_backward_walk(a, st)) != cudaSuccess) return cuda_fail(ctx, e);
-        if ((e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
+        if (grad_queries &&
+            (e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
             return cuda_fail(ctx, e);
     }
     if (!reuse) ctx->key.valid = false;
     return SDTW_OK;
+}
+
+sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
+                          int32_t B, int32_t N, const int64_t* end, const float* grad_cost, float* grad_queries,
+                          float* grad_ref, int32_t* path, void* stream)
+{
+    if (!ctx) return SDTW_E_INVALID;
+    if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
+    if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, end, grad_cost);
+    if (s != SDTW_OK) return s;
+    if (B > 0 && (!grad_queries || !grad_ref)) return SDTW_E_INVALID;
+    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B == 0) {
+        if (!grad_ref) return SDTW_E_INVALID;
+        cudaError_t e = cudaMemsetAsync(grad_ref, 0, 4 * static_cast<size_t>(M), st);
+        return e == cudaSuccess ? SDTW_OK : cuda_fail(ctx, e);
+    }
+    return run_backward(ctx, ref, M, queries, offsets, B, N, end, grad_cost, grad_queries, grad_ref, path, st);
+}
+
+sdtw_status sdtw_path(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
+                      int32_t B, int32_t N, const int64_t* end, int32_t* path, void* stream)
+{
+    if (!ctx) return SDTW_E_INVALID;
+    if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
+    if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    sdtw_status s = check_common(ctx, ref, M, queries, B, N, end, path);
+    if (s != SDTW_OK) return s;
+    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
+    if (B == 0) return SDTW_OK;
+    return run_backward(ctx, ref, M, queries, offsets, B, N, end, nullptr, nullptr, nullptr, path,
+                        static_cast<cudaStream_t>(stream));
 }
 
 sdtw_status sdtw_forward_host(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,

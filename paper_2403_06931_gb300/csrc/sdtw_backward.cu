@@ -120,11 +120,12 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         }
         return;
     }
-    const float g2 = 2.f * a.grad_cost[q];
+    const bool grads = a.grad_queries != nullptr;  // false: the path only
+    const float g2 = grads ? 2.f * a.grad_cost[q] : 0.f;
     const float* x = a.queries + start;
     for (int i = lane; i < n; i += 32) xs[i] = x[i];
     float* gyq = a.gyq + static_cast<int64_t>(ql) * a.M;
-    float* gq = a.grad_queries + start;
+    float* gq = grads ? a.grad_queries + start : nullptr;
     int32_t* path = a.path ? a.path + 2 * start : nullptr;
 
     // the forward's schedule for this query (sdtw_forward.cu)
@@ -316,8 +317,10 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
                 // the path starts here: only this cell of row 0 is on it
                 const float cg = g2 * (xi - ys[wj - c0]);
                 if (lane == 0) {
-                    gq[0] = ax + cg;
-                    gyq[wj] = ay - cg;
+                    if (grads) {
+                        gq[0] = ax + cg;
+                        gyq[wj] = ay - cg;
+                    }
                     if (path) path[0] = wj;
                     a.span[2 * ql] = wj;
                     a.span[2 * ql + 1] = e64;
@@ -349,14 +352,14 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
             float vy = -cg;
             if (lane == 0) vy += ay;
             const int lcode = (lane == last && fcode != kOutside && f < 32) ? fcode : kLeft;
-            if (on && lcode != kUp) gyq[jk] = vy;
+            if (grads && on && lcode != kUp) gyq[jk] = vy;
             const float vlast = __shfl_sync(0xffffffffu, vy, last);
             ay = (f < 32 && fcode == kUp) ? vlast : 0.f;
             if (f < 32 && fcode != kOutside) {
                 // the row ends at (wi, wj - last); move up or diagonally
                 const int jl = wj - last;
                 if (lane == 0) {
-                    gq[wi] = ax;
+                    if (grads) gq[wi] = ax;
                     if (path) path[2 * wi] = jl;
                 }
                 ax = 0.f;

@@ -43,6 +43,13 @@ def random_walk(rng: np.random.Generator, n: int) -> np.ndarray:
     return np.cumsum(rng.standard_normal(int(n)))
 
 
+def random_walks(B: int, n: int, seed: int) -> np.ndarray:
+    """B raw (not normalised) float32 random walks of length n: the input of a
+    batch z-normalisation."""
+    rng = rng_for(SEED_BASE + seed)
+    return np.stack([random_walk(rng, n) for _ in range(B)]).astype(np.float32)
+
+
 def znorm(v: np.ndarray) -> np.ndarray:
     """Eq. 2 standardisation in float64: (v - mean) / S with population S.
 

@@ -107,6 +107,17 @@ class SdtwContext:
         capi.check(st, "sdtw_backward", self.handle)
         return gq, gr, path
 
+    def path(self, ref, queries, end, offsets=None, N=None, stream=None, out=None):
+        """Per query row, the first and last column of the warp path (sdtw_path):
+        int32 [total samples, 2]."""
+        self._check(ref, queries, offsets, end)
+        B, N, M = self._dims(ref, queries, offsets, N)
+        path = out if out is not None else torch.empty(queries.numel() * 2, dtype=torch.int32, device=ref.device)
+        st = capi.sdtw_path(self.handle, _ptr(ref), M, _ptr(queries), _ptr(offsets), B, N, _ptr(end), _ptr(path),
+                            _stream_ptr(stream))
+        capi.check(st, "sdtw_path", self.handle)
+        return path.view(-1, 2)
+
     def autotune(self, ref, queries, offsets=None, N=None, stream=None):
         """Time the candidate plans on this batch and keep the fastest (sdtw_autotune)."""
         self._check(ref, queries, offsets)
@@ -162,6 +173,26 @@ class SdtwFunction(torch.autograd.Function):
         gq, gr, _ = fctx.sctx.backward(ref, queries, end, grad_cost.contiguous(), offsets=fctx.offsets,
                                        N=fctx.N)
         return gr, gq, None, None, None
+
+
+def znormalize(x, offsets=None, out=None, stream=None):
+    """Eq. 2 z-normalisation of a batch (sdtw_znormalize): x is [B, N] (or 1-D
+    with offsets [B+1]), float32 on a CUDA device; returns out (in place if
+    out is x)."""
+    if not x.is_cuda or not x.is_contiguous() or x.dtype != torch.float32:
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    if offsets is None:
+        if x.dim() == 1:
+            B, N = 1, x.numel()
+        else:
+            B, N = x.shape
+    else:
+        B, N = offsets.numel() - 1, 1
+    if out is None:
+        out = torch.empty_like(x)
+    st = capi.sdtw_znormalize(_ptr(x), _ptr(out), _ptr(offsets), int(B), int(N), _stream_ptr(stream))
+    capi.check(st, "sdtw_znormalize")
+    return out
 
 
 def sdtw_cost(ref, queries, ctx: SdtwContext, offsets=None, N=None):

@@ -200,6 +200,25 @@ def test_chunked_and_recomputed_backward_are_identical(gpu):
         run_bwd(gpu, w, keep=False, mem_cap_bytes=fixed + 4 * per_q // 2, **st)
 
 
+def test_path_entry_point_matches_backward(gpu):
+    # sdtw_path: the walk-back without gradients, from kept checkpoints and from
+    # a re-run forward, equals the backward's path
+    for w in (inputs.tiny(B=6, N=300, M=5000, seed=87), inputs.ragged_fp32(B=5, n_lo=1, n_hi=400, M=3000, seed=88)):
+        cost, end, gq, gr, path, g = run_bwd(gpu, w)
+        ref = torch.from_numpy(w.ref).to(gpu)
+        qs = torch.from_numpy(w.queries).to(gpu)
+        offs = torch.from_numpy(w.offsets).to(gpu) if w.offsets is not None else None
+        Nq = int(w.lengths.max())
+        for keep in (True, False):
+            ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=Nq, max_total_query_len=qs.numel(),
+                              grad=True, keep_checkpoints=keep)
+            c2, e2 = ctx.forward(ref, qs, offsets=offs, N=Nq if offs is not None else None)
+            p2 = ctx.path(ref, qs, e2, offsets=offs, N=Nq if offs is not None else None)
+            assert ctx.device_status() == capi.SDTW_OK
+            assert np.array_equal(e2.cpu().numpy(), end) and np.array_equal(p2.cpu().numpy(), path)
+            ctx.close()
+
+
 def test_host_forward_backward_matches_device(gpu):
     w = inputs.tiny(B=5, N=120, M=2000, seed=91)
     cost, end, gq, gr, path, g = run_bwd(gpu, w)

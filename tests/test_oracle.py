@@ -325,3 +325,51 @@ def test_interval_validity_rejects_bad_runs(oracle_mod):
     assert not oracle_mod.intervals_are_valid([1, 2, 2], [1, 3, 4], 5, 4)   # run overlaps previous row
     assert not oracle_mod.intervals_are_valid([1, 2, 4], [1, 1, 4], 5, 4)   # lo > hi
     assert not oracle_mod.intervals_are_valid([1, 2, 4], [1, 3, 5], 5, 5)   # outside the matrix
+
+
+# --------------------------------------------------- z-normalisation (Eq. 2) --
+
+def test_znorm_textbook_example(oracle_mod):
+    # the classic population example: mean 5, population standard deviation 2
+    z = oracle_mod.znormalize([2, 4, 4, 4, 5, 5, 7, 9])
+    assert np.array_equal(z, [-1.5, -0.5, -0.5, -0.5, 0.0, 0.0, 1.0, 2.0])
+    z3 = oracle_mod.znormalize([1, 2, 3])
+    s = np.sqrt(2.0 / 3.0)                       # population, not the sample sqrt(1)
+    assert np.allclose(z3, [-1 / s, 0.0, 1 / s], rtol=0, atol=1e-15)
+
+
+def test_znorm_moments_and_library(oracle_mod):
+    x = np.random.default_rng(3).standard_normal(1000) * 3.0 + 1.5
+    z = oracle_mod.znormalize(x)
+    assert abs(z.mean()) < 1e-12 and abs(np.mean(z * z) - 1.0) < 1e-12
+    assert np.allclose(z, (x - x.mean()) / x.std(ddof=0), rtol=1e-13, atol=1e-13)
+
+
+def test_znorm_affine_invariance(oracle_mod):
+    x = np.random.default_rng(4).standard_normal(257)
+    z = oracle_mod.znormalize(x)
+    assert np.allclose(oracle_mod.znormalize(3.0 * x + 7.0), z, rtol=0, atol=1e-12)
+    assert np.allclose(oracle_mod.znormalize(-2.0 * x + 1.0), -z, rtol=0, atol=1e-12)
+
+
+def test_znorm_degenerate_series(oracle_mod):
+    assert np.array_equal(oracle_mod.znormalize([4.25] * 9), np.zeros(9))   # zero spread: centred only
+    assert np.array_equal(oracle_mod.znormalize([-3.0]), [0.0])
+    assert oracle_mod.znormalize(np.zeros(0)).size == 0
+
+
+def test_znorm_is_two_pass(oracle_mod):
+    # a large common offset: the centred second moment keeps the digits that
+    # a one-pass E[x^2] - E[x]^2 would cancel away
+    noise = np.random.default_rng(5).standard_normal(4000)
+    z = oracle_mod.znormalize(1e9 + noise)
+    assert np.allclose(z, oracle_mod.znormalize(noise), rtol=0, atol=1e-6)
+
+
+def test_znorm_batch_layouts(oracle_mod):
+    v = np.random.default_rng(6).standard_normal(30)
+    u = oracle_mod.znormalize_batch(v, N=10)
+    assert np.array_equal(u[10:20], oracle_mod.znormalize(v[10:20]))
+    offs = np.array([0, 3, 3, 17, 30])
+    r = oracle_mod.znormalize_batch(v, offsets=offs)
+    assert np.array_equal(r[3:17], oracle_mod.znormalize(v[3:17])) and np.array_equal(r[17:], oracle_mod.znormalize(v[17:]))
