@@ -115,6 +115,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ ours --
 
+def max_over_ranks(value, world, dev):
+    """The largest of a per-rank value over all ranks (the job's step time is
+    its slowest rank's); a plain float when running alone."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = t.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gcups(world, cells_per_rank, step_ms_max):
+    """Whole-job throughput: every rank processes its own batch of cells_per_rank
+    cells (weak scaling, no collective on the data path) in at most step_ms_max."""
+    return world * cells_per_rank / (step_ms_max * 1e-3) / 1e9
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -189,11 +207,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = sum(fwd_ms) / args.steps + sum(bwd_ms) / args.steps
     if ctx.device_status() != capi.SDTW_OK:
         raise RuntimeError("device status error in the timed region")
-    t = torch.tensor([step_ms], dtype=torch.float64)
-    if world > 1:
-        t = t.to(dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
+    step_ms_max = max_over_ranks(step_ms, world, dev)
     clocks = clk.summary()
 
     # e2e: host buffers through the C ABI, copies inside the timed region
@@ -249,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = round(achieved / (sms * LANES_PER_SM * clocks["sm_mhz"] * 1e6
                                                           / OPS_PER_CELL / 1e9), 4)
-    value = world * cells / (step_ms_max * 1e-3) / 1e9
+    value = job_gcups(world, cells, step_ms_max)
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms_max, 3), "higher_is_better": True,
