@@ -1,9 +1,12 @@
 """GPU batch z-normalisation (sdtw_znormalize, paper Section 5.1, Eq. 2)
 against the FP64 oracle, element by element.
 
-The kernel accumulates in double and rounds once to float, so every output is
-within one float rounding of the oracle's value: |z - o| <= 2^-23 |o| plus a
-1e-12 floor for outputs near zero.
+The kernel keeps the per-sample arithmetic in float (compensated sums of the
+samples shifted by the first one, the mean as a float pair, the centred values
+as (x - hi) - lo) and combines partial sums in double.  Each output then
+carries a few float roundings at the scale of max(|z|, 1): the bound checked
+is |z - o| <= 2^-21 (|o| + 1).  (A float32 emulation of the kernel on random
+walks, offsets of 1e4 and 1e6 and long series stays below 2.7e-7.)
 """
 import numpy as np
 import pytest
@@ -18,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 def _check(z, o):
     z = np.asarray(z, dtype=np.float64)
-    bad = np.abs(z - o) > 2.0 ** -23 * np.abs(o) + 1e-12
+    bad = np.abs(z - o) > 2.0 ** -21 * (np.abs(o) + 1.0)
     assert not bad.any(), (int(np.argmax(bad)), z[bad][:3], o[bad][:3])
 
 
