@@ -246,9 +246,9 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
  * Batch z-normalisation (paper Section 5.1, Eq. 2): each series becomes
  * (x - mean) / S with its own mean and population standard deviation S (the
  * paper's code divides by n); a series with S == 0 is only centred.  Two
- * passes (the mean, then the centred second moment), per-sample arithmetic in
- * float with compensated sums, partial sums combined in double: every output
- * is within 2^-21 (|z| + 1) of the exact value.  This is the standardisation
+ * passes (the mean, then the centred second moment) in float with compensated
+ * sums and float-pair reductions: every output is within 2^-21 (|z| + 1) of
+ * the exact value.  This is the standardisation
  * the forward expects of its inputs (the library does not apply it
  * implicitly).
  *   in, out   device float: B series back to back, [B][N] or delimited by

@@ -8,16 +8,19 @@
 // warp (short series) or one CTA (long series) per series makes two
 // reduction passes, the mean and then the centred second moment: the one-pass
 // difference cancels digits when the mean is large against the spread.  FP64
-// throughput is a small fraction of FP32 on this part, so the per-sample work
-// stays in FP32 without losing accuracy:
+// runs at a small fraction of the FP32 rate on this part (a version with
+// double reductions spent most of its time in them), so everything is FP32,
+// with compensated float pairs (hi + lo) where one float is not enough:
 //   * each lane sums x - x[0] (shifting by the series' first sample removes a
-//     large common offset) with Kahan compensation, and only the lanes'
-//     (sum, compensation) pairs are combined in double;
-//   * the mean is carried as a pair of floats (hi + lo), and every sample is
-//     centred as (x - hi) - lo, so the centred values are accurate to about
-//     one float rounding; their squares are again Kahan-summed per lane.
-// The series is read three times (the second and third reads hit L2 for
-// query-sized series), so HBM sees one read and one write per sample.
+//     large common offset) with Kahan compensation, and the lanes' partial
+//     sums are combined as float pairs (error-free TwoSum);
+//   * the mean is the float pair x[0] + S/n (a pair division by n), and every
+//     sample is centred as (x - hi) - lo, accurate to about one float rounding;
+//     the centred squares are again Kahan-summed and pair-reduced; the scale is
+//     1 / sqrt(variance) in float.
+// Series of up to 2,048 samples stay in the warp's registers between the
+// passes; longer ones are read three times (the second and third reads hit
+// L2 for query-sized series).  HBM sees one read and one write per sample.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,7 +32,40 @@ namespace {
 constexpr int kNormThreads = 256;
 constexpr int kWarpMaxN = 16384;  // uniform series up to this length take one warp each
 
-// Kahan-compensated running sum
+// A value carried as an unevaluated sum of two floats, hi + lo.
+struct FF {
+    float hi, lo;
+};
+
+// error-free sums (TwoSum; FastTwoSum when |a| >= |b|)
+__device__ __forceinline__ FF two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const FF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+// a / n for a count n (the remainder of the first quotient is exact by FMA)
+__device__ __forceinline__ FF ff_div(FF a, float n)
+{
+    const float q1 = a.hi / n;
+    const float r = fmaf(-q1, n, a.hi) + a.lo;
+    return fast_two_sum(q1, r / n);
+}
+
+// Kahan-compensated running sum; its value is the pair (s, -c)
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v)
@@ -39,57 +75,62 @@ struct KSum {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double value() const { return static_cast<double>(s) - static_cast<double>(c); }
+    __device__ __forceinline__ FF value() const { return {s, -c}; }
 };
 
-__device__ __forceinline__ double warp_sum(double v)
+__device__ __forceinline__ FF warp_sum(FF v)
 {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    for (int off = 16; off > 0; off >>= 1)
+        v = ff_add(v, FF{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)});
     return v;
 }
 
-// sum over the CTA of one double per thread, returned to every thread
-__device__ __forceinline__ double block_sum(double v, double* red)
+// sum over the CTA of one pair per thread, returned to every thread
+__device__ __forceinline__ FF block_sum(FF v, FF* red)
 {
     v = warp_sum(v);
     __syncthreads();  // red[] may still be read by the previous reduction
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = 0.0;
+    FF t = red[0];
 #pragma unroll
-    for (int w = 0; w < kNormThreads / 32; ++w) t += red[w];
+    for (int w = 1; w < kNormThreads / 32; ++w) t = ff_add(t, red[w]);
     return t;
 }
 
+// the scale 1 / S from the sum of squares (1 when the spread is zero)
+__device__ __forceinline__ float inv_spread(FF sq, float n)
+{
+    const float var = ff_div(sq, n).hi;
+    return var > 0.f ? 1.f / sqrtf(var) : 1.f;
+}
+
 // Eq. 2 on one series of n samples at x (written to z), by `count` threads
-// with index `idx`; REDUCE sums a double over those threads.
+// with index `idx`; REDUCE sums a pair over those threads.
 template <typename Reduce>
 __device__ __forceinline__ void znorm_series(const float* x, float* z, int64_t n, int idx, int count, Reduce reduce)
 {
     const float x0 = x[0];
+    const float nf = static_cast<float>(n);
     KSum s1;
     for (int64_t i = idx; i < n; i += count) s1.add(x[i] - x0);
-    const double mean = static_cast<double>(x0) + reduce(s1.value()) / static_cast<double>(n);
-    const float hi = static_cast<float>(mean);
-    const float lo = static_cast<float>(mean - static_cast<double>(hi));
+    const FF mean = ff_add(FF{x0, 0.f}, ff_div(reduce(s1.value()), nf));
     KSum s2;
     for (int64_t i = idx; i < n; i += count) {
-        const float c = (x[i] - hi) - lo;
+        const float c = (x[i] - mean.hi) - mean.lo;
         s2.add(c * c);
     }
-    double sd = sqrt(reduce(s2.value()) / static_cast<double>(n));
-    if (!(sd > 0.0)) sd = 1.0;
-    const float inv = static_cast<float>(1.0 / sd);
+    const float inv = inv_spread(reduce(s2.value()), nf);
     // each thread rewrites only elements it read itself: safe in place
-    for (int64_t i = idx; i < n; i += count) z[i] = ((x[i] - hi) - lo) * inv;
+    for (int64_t i = idx; i < n; i += count) z[i] = ((x[i] - mean.hi) - mean.lo) * inv;
 }
 
 // one CTA per series: long series, and ragged batches (lengths on the device)
 __global__ void __launch_bounds__(kNormThreads)
 znorm_kernel(const float* in, float* out, const int64_t* offsets, int32_t N)
 {
-    __shared__ double red[kNormThreads / 32];
+    __shared__ FF red[kNormThreads / 32];
     const int q = blockIdx.x;
     int64_t a, n;
     if (offsets) {
@@ -100,7 +141,7 @@ znorm_kernel(const float* in, float* out, const int64_t* offsets, int32_t N)
         a = static_cast<int64_t>(q) * N;
         n = N;
     }
-    znorm_series(in + a, out + a, n, threadIdx.x, kNormThreads, [&](double v) { return block_sum(v, red); });
+    znorm_series(in + a, out + a, n, threadIdx.x, kNormThreads, [&](FF v) { return block_sum(v, red); });
 }
 
 // The same with 16-byte loads and stores: series of a multiple of 4 samples
@@ -108,6 +149,7 @@ znorm_kernel(const float* in, float* out, const int64_t* offsets, int32_t N)
 __device__ __forceinline__ void znorm_series_v4(const float4* x, float4* z, int n4, int lane)
 {
     const float x0 = reinterpret_cast<const float*>(x)[0];
+    const float nf = 4.f * n4;
     KSum s1;
     for (int i = lane; i < n4; i += 32) {
         const float4 v = x[i];
@@ -116,10 +158,8 @@ __device__ __forceinline__ void znorm_series_v4(const float4* x, float4* z, int 
         s1.add(v.z - x0);
         s1.add(v.w - x0);
     }
-    const double n = 4.0 * n4;
-    const double mean = static_cast<double>(x0) + warp_sum(s1.value()) / n;
-    const float hi = static_cast<float>(mean);
-    const float lo = static_cast<float>(mean - static_cast<double>(hi));
+    const FF mean = ff_add(FF{x0, 0.f}, ff_div(warp_sum(s1.value()), nf));
+    const float hi = mean.hi, lo = mean.lo;
     KSum s2;
     for (int i = lane; i < n4; i += 32) {
         const float4 v = x[i];
@@ -129,14 +169,64 @@ __device__ __forceinline__ void znorm_series_v4(const float4* x, float4* z, int 
         s2.add(c2 * c2);
         s2.add(c3 * c3);
     }
-    double sd = sqrt(warp_sum(s2.value()) / n);
-    if (!(sd > 0.0)) sd = 1.0;
-    const float inv = static_cast<float>(1.0 / sd);
+    const float inv = inv_spread(warp_sum(s2.value()), nf);
     for (int i = lane; i < n4; i += 32) {
         const float4 v = x[i];
         z[i] = make_float4(((v.x - hi) - lo) * inv, ((v.y - hi) - lo) * inv, ((v.z - hi) - lo) * inv,
                            ((v.w - hi) - lo) * inv);
     }
+}
+
+// The same for a series of up to 32 * 4 * kRegVec4 samples held in the warp's
+// registers: one read and one write per sample, no second or third pass over
+// memory.
+constexpr int kRegVec4 = 16;  // float4 per lane: series of up to 2,048 samples
+
+__device__ __forceinline__ void znorm_series_regs(const float4* x, float4* z, int n4, int lane)
+{
+    float4 v[kRegVec4];
+#pragma unroll
+    for (int k = 0; k < kRegVec4; ++k)
+        v[k] = lane + 32 * k < n4 ? x[lane + 32 * k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float x0 = __shfl_sync(0xffffffffu, v[0].x, 0);
+    const float nf = 4.f * n4;
+    KSum s1;
+#pragma unroll
+    for (int k = 0; k < kRegVec4; ++k) {
+        if (lane + 32 * k < n4) {
+            s1.add(v[k].x - x0);
+            s1.add(v[k].y - x0);
+            s1.add(v[k].z - x0);
+            s1.add(v[k].w - x0);
+        }
+    }
+    const FF mean = ff_add(FF{x0, 0.f}, ff_div(warp_sum(s1.value()), nf));
+    const float hi = mean.hi, lo = mean.lo;
+    KSum s2;
+#pragma unroll
+    for (int k = 0; k < kRegVec4; ++k) {
+        v[k] = make_float4((v[k].x - hi) - lo, (v[k].y - hi) - lo, (v[k].z - hi) - lo, (v[k].w - hi) - lo);
+        if (lane + 32 * k < n4) {
+            s2.add(v[k].x * v[k].x);
+            s2.add(v[k].y * v[k].y);
+            s2.add(v[k].z * v[k].z);
+            s2.add(v[k].w * v[k].w);
+        }
+    }
+    const float inv = inv_spread(warp_sum(s2.value()), nf);
+#pragma unroll
+    for (int k = 0; k < kRegVec4; ++k)
+        if (lane + 32 * k < n4) z[lane + 32 * k] = make_float4(v[k].x * inv, v[k].y * inv, v[k].z * inv, v[k].w * inv);
+}
+
+__global__ void __launch_bounds__(kNormThreads)
+znorm_warp_regs_kernel(const float* in, float* out, int32_t B, int32_t N)
+{
+    const int q = blockIdx.x * (kNormThreads / 32) + (threadIdx.x >> 5);
+    if (q >= B) return;
+    const int64_t a = static_cast<int64_t>(q) * N;
+    znorm_series_regs(reinterpret_cast<const float4*>(in + a), reinterpret_cast<float4*>(out + a), N / 4,
+                      threadIdx.x & 31);
 }
 
 // one warp per series (eight series per CTA): no CTA barrier
@@ -150,7 +240,7 @@ znorm_warp_kernel(const float* in, float* out, int32_t B, int32_t N, bool vec4)
         znorm_series_v4(reinterpret_cast<const float4*>(in + a), reinterpret_cast<float4*>(out + a), N / 4,
                         threadIdx.x & 31);
     else
-        znorm_series(in + a, out + a, N, threadIdx.x & 31, 32, [](double v) { return warp_sum(v); });
+        znorm_series(in + a, out + a, N, threadIdx.x & 31, 32, [](FF v) { return warp_sum(v); });
 }
 
 }  // namespace
@@ -168,7 +258,10 @@ extern "C" sdtw_status sdtw_znormalize(const float* in, float* out, const int64_
         const int per = kNormThreads / 32;
         const bool vec4 = N % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
                           reinterpret_cast<uintptr_t>(out) % 16 == 0;
-        znorm_warp_kernel<<<(B + per - 1) / per, kNormThreads, 0, st>>>(in, out, B, N, vec4);
+        if (vec4 && N <= 32 * 4 * kRegVec4)
+            znorm_warp_regs_kernel<<<(B + per - 1) / per, kNormThreads, 0, st>>>(in, out, B, N);
+        else
+            znorm_warp_kernel<<<(B + per - 1) / per, kNormThreads, 0, st>>>(in, out, B, N, vec4);
     } else {
         znorm_kernel<<<B, kNormThreads, 0, st>>>(in, out, offsets, N);
     }

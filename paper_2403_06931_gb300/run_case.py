@@ -31,7 +31,11 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--keep-checkpoints", action="store_true",
                     help="the forward stores backward checkpoints (implied by --backward)")
+    ap.add_argument("--znorm", action="store_true",
+                    help="time the batch z-normalisation (Eq. 2) of B x N raw random walks instead of the fill")
     a = ap.parse_args()
+    if a.znorm:
+        return run_znorm(a)
 
     kw = {k: v for k, v in (("B", a.B), ("N", a.N), ("M", a.M)) if v is not None}
     if a.workload == "ragged":
@@ -76,6 +80,26 @@ def main():
     ctx.close()
     if status != 0:
         raise SystemExit(f"device status {status}")
+
+
+def run_znorm(a):
+    from .sdtw import znormalize
+    B, N = a.B or 512, a.N or 2000
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.from_numpy(inputs.random_walks(B, N, seed=11)).to(dev)
+    z = torch.empty_like(x)
+    times = []
+    for rep in range(a.reps + 1):  # the first run is an untimed warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        znormalize(x, out=z)
+        e1.record()
+        e1.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    print(json.dumps({"workload": f"znorm_{B}x{N}", "B": B, "N": N, "ms": round(ms, 4),
+                      "gbs": round(8 * B * N / (ms * 1e-3) / 1e9, 1)}))
 
 
 if __name__ == "__main__":

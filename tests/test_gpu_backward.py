@@ -219,6 +219,44 @@ def test_path_entry_point_matches_backward(gpu):
             ctx.close()
 
 
+def test_differentiable_step_replays_from_a_cuda_graph(gpu):
+    # forward with checkpoints + backward allocate nothing after the context is
+    # created, so the whole step can be captured once and replayed
+    w = inputs.tiny(B=6, N=300, M=6000, seed=89)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True, keep_checkpoints=True)
+    cost = torch.empty(w.B, device=gpu)
+    end = torch.empty(w.B, dtype=torch.int64, device=gpu)
+    g = torch.linspace(0.5, 1.5, w.B, device=gpu)
+    gq = torch.empty_like(qs)
+    gr = torch.empty_like(ref)
+    path = torch.empty(qs.numel() * 2, dtype=torch.int32, device=gpu)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+
+    def step():
+        ctx.forward(ref, qs, out=(cost, end), stream=s)
+        ctx.backward(ref, qs, end, g, out=(gq, gr, path), stream=s)
+
+    with torch.cuda.stream(s):
+        step()                                   # warm-up outside the capture
+    torch.cuda.synchronize()
+    want = [t.clone() for t in (cost, end, gq, gr, path)]
+    for t in (cost, gq, gr):
+        t.fill_(float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        step()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert ctx.device_status() == capi.SDTW_OK
+    for a, b in zip(want, (cost, end, gq, gr, path)):
+        assert torch.equal(a, b)
+    ctx.close()
+
+
 def test_host_forward_backward_matches_device(gpu):
     w = inputs.tiny(B=5, N=120, M=2000, seed=91)
     cost, end, gq, gr, path, g = run_bwd(gpu, w)

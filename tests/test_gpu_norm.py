@@ -1,9 +1,9 @@
 """GPU batch z-normalisation (sdtw_znormalize, paper Section 5.1, Eq. 2)
 against the FP64 oracle, element by element.
 
-The kernel keeps the per-sample arithmetic in float (compensated sums of the
-samples shifted by the first one, the mean as a float pair, the centred values
-as (x - hi) - lo) and combines partial sums in double.  Each output then
+The kernel works in float only: compensated sums of the samples shifted by the
+first one, reductions and the mean as float pairs (hi + lo), the centred values
+as (x - hi) - lo.  Each output then
 carries a few float roundings at the scale of max(|z|, 1): the bound checked
 is |z - o| <= 2^-21 (|o| + 1).  (A float32 emulation of the kernel on random
 walks, offsets of 1e4 and 1e6 and long series stays below 2.7e-7.)
@@ -59,9 +59,11 @@ def test_in_place_and_long_series(gpu):
     _check(t.cpu().numpy(), oracle.znormalize(x))
 
 
-@pytest.mark.parametrize("N", [1, 2, 33, 16384, 16385])
+@pytest.mark.parametrize("N", [1, 2, 4, 33, 2048, 2052, 16384, 16385])
 def test_uniform_lengths_across_kernels(gpu, N):
-    # series up to 16,384 samples take a warp each, longer ones a CTA each
+    # series of a multiple of 4 samples up to 2,048 stay in a warp's registers,
+    # others up to 16,384 take a warp each (16-byte accesses when N % 4 == 0),
+    # longer ones a CTA each
     x = _walks(9, N, 10 + N, offset=1.0)
     x[4] = 2.5                                # a constant series
     z = znormalize(torch.from_numpy(x).to(gpu)).cpu().numpy()
