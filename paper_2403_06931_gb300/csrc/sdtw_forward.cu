@@ -47,16 +47,18 @@
 // drift falls below 1e-7 and the worst error to ~1.5e-6.
 //
 // Optional checkpoints for the backward pass (a separate instantiation, so the
-// plain forward carries none of it).  At the start of every chunk, right after
-// the rebase, every thread stores its state: the strip's latest row relative
-// to its base, the right-hand cells of its tile's other rows, its diagonal
-// input and the base.  Since thread l is one tile behind thread l-1, the rows
-// stored at one chunk start form an anti-diagonal staircase, the wavefront;
-// all lanes store on the same step, so the stores are whole-warp and
-// coalesced.  The strip whose first column is a multiple of K also stores the
-// left inputs it uses, already converted into its own base.  From a chunk's
-// wavefront and those columns the backward recomputes any K-column window of
-// the chunk with the forward's own operations, bit for bit.
+// plain forward carries none of it).  At the end of every chunk every thread
+// stores its state as the next chunk will find it before its rebase: the
+// strip's latest row relative to its base, the right-hand cells of its tile's
+// other rows, its diagonal input and the base (the backward redoes the
+// rebase).  Since thread l is one tile behind thread l-1, the rows stored at
+// one chunk end form an anti-diagonal staircase, the wavefront; all lanes
+// store on the same step, so the stores are whole-warp and coalesced.  The
+// strip whose first column is a multiple of K also stores the left inputs it
+// uses, already converted into its own base.  From a chunk's wavefront and
+// those columns the backward recomputes any K-column window of the chunk with
+// the forward's own operations, bit for bit.  Checkpoints go out with the
+// streaming (evict-first) store hint.
 #include <cuda_runtime.h>
 
 #include <algorithm>
