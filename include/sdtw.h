@@ -117,8 +117,10 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * SDTW_FLAG_GRAD is set), sized from the cfg maxima and allocated here.
  * *out receives the context, or NULL on error.
  * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
- * SDTW_FLAG_GRAD with SDTW_I8), SDTW_E_NOMEM (workspace above mem_cap_bytes or
- * allocation failure), SDTW_E_CUDA (device unusable). */
+ * SDTW_FLAG_GRAD with SDTW_I8, an unsupported seg_width or tile_rows, a
+ * non-zero reserved0), SDTW_E_UNSUPPORTED (a ckpt_stride other than 0 or 32),
+ * SDTW_E_NOMEM (workspace above mem_cap_bytes, too small for one query's
+ * checkpoints, or allocation failure), SDTW_E_CUDA (device unusable). */
 sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg);
 
 /* Release the context and its workspace (synchronises its device first).
@@ -140,7 +142,9 @@ sdtw_status sdtw_destroy(sdtw_ctx* ctx);
  *   cost     device, B elements: float (SDTW_F32) or int32 (SDTW_I8).
  *   end      device int64, B elements: the smallest column of the minimum.
  * With SDTW_FLAG_KEEP_CHECKPOINTS the call also stores the checkpoints a
- * following sdtw_backward on the same arguments reuses.
+ * following sdtw_backward (or sdtw_path) on the same arguments reuses, when
+ * the whole batch's checkpoints fit the context's workspace (otherwise the
+ * backward re-runs the forward in chunks of queries).
  * Errors: SDTW_E_INVALID (null pointers with B > 0, N < 1, M < 1, sizes above
  * the context maxima; SDTW_I8 needs N <= 33,000 so int32 costs cannot
  * overflow), SDTW_E_UNSUPPORTED (N too long for shared memory), SDTW_E_CUDA.
