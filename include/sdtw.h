@@ -75,7 +75,8 @@ typedef struct sdtw_config {
     int64_t max_total_query_len; /* largest total query samples per call (B*N, or offsets[B]) */
     int32_t max_batch;           /* largest B */
     int32_t max_query_len;       /* largest N (the longest query of a ragged batch) */
-    int32_t seg_width;           /* reference columns per thread (the paper's segment width); 0 = chosen by the library */
+    int32_t seg_width;           /* reference columns per thread (the paper's segment width): 8, 16, 20, 24, 28
+                                    or 32; 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
     int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints; 0 = 32 (the only stride this build has) */
     int32_t reserved0;           /* must be 0 */

@@ -50,7 +50,11 @@ struct DirWord<2> { using T = uint8_t; };
 template <>
 struct DirWord<4> { using T = uint8_t; };
 template <>
+struct DirWord<5> { using T = uint16_t; };
+template <>
 struct DirWord<6> { using T = uint16_t; };
+template <>
+struct DirWord<7> { using T = uint16_t; };
 template <>
 struct DirWord<8> { using T = uint16_t; };
 
@@ -403,7 +407,7 @@ cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 
 }  // namespace
 
-bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
+bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 20 || W == 24 || W == 28 || W == 32; }
 
 int bwd_smem_bytes(int N, int W, int RT)
 {
@@ -420,7 +424,9 @@ cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)
     switch (a.W) {
     case 8: return launch_walk_wb<2>(a, s);
     case 16: return launch_walk_wb<4>(a, s);
+    case 20: return launch_walk_wb<5>(a, s);
     case 24: return launch_walk_wb<6>(a, s);
+    case 28: return launch_walk_wb<7>(a, s);
     case 32: return launch_walk_wb<8>(a, s);
     default: return cudaErrorInvalidValue;
     }

@@ -177,7 +177,7 @@ template <int WRT>
 constexpr int fwd_reg_cap()
 {
     constexpr int W = WRT / 8, RT = WRT % 8;
-    return W <= 8 ? (RT == 2 ? 72 : 80) : W <= 16 ? (RT == 2 ? 88 : 96) : W <= 24 ? (RT == 2 ? 112 : 120) : 128;
+    return W <= 8 ? (RT == 2 ? 72 : 80) : W <= 16 ? (RT == 2 ? 88 : 96) : W <= 20 ? (RT == 2 ? 104 : 112) : W <= 24 ? (RT == 2 ? 112 : 120) : 128;
 }
 
 template <typename Tin, int W, int RT, bool CKPT>
@@ -557,7 +557,9 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
     switch (W) {                                                          \
     case 8: return f(Inst<Tin, 8, RTv, CK>{});                            \
     case 16: return f(Inst<Tin, 16, RTv, CK>{});                          \
+    case 20: return f(Inst<Tin, 20, RTv, CK>{});                          \
     case 24: return f(Inst<Tin, 24, RTv, CK>{});                          \
+    case 28: return f(Inst<Tin, 28, RTv, CK>{});                          \
     case 32: return f(Inst<Tin, 32, RTv, CK>{});                          \
     default: return cudaErrorInvalidValue;                                \
     }
@@ -575,7 +577,7 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 
 }  // namespace
 
-bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 24 || W == 32; }
+bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 20 || W == 24 || W == 28 || W == 32; }
 
 int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT)
 {

@@ -144,7 +144,7 @@ def test_backward_shapes(gpu, B, N, M, W, RT, P):
 
 
 @pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 16, 24, 32])
+@pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
 def test_backward_every_tile_height_and_width(gpu, RT, W):
     # checkpoints taken by every checkpointing forward variant
     w = inputs.tiny(B=3, N=700, M=9000, seed=400 + RT + W)

@@ -53,7 +53,7 @@ def test_shapes_fp32(gpu, B, N, M):
 
 
 @pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 16, 24, 32])
+@pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
 @pytest.mark.parametrize("P", [1, 2, 3, 4, 8, 16])
 def test_every_plan_fp32(gpu, W, P, RT):
     w = inputs.tiny(B=3, N=91, M=6000, seed=77)
@@ -62,7 +62,7 @@ def test_every_plan_fp32(gpu, W, P, RT):
 
 
 @pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 16, 24, 32])
+@pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
 @pytest.mark.parametrize("P", [1, 4, 16])
 def test_every_plan_i8_bit_exact(gpu, W, P, RT):
     w = inputs.paper_i8(B=4, N=70, M=5000, seed=78)
@@ -72,7 +72,7 @@ def test_every_plan_i8_bit_exact(gpu, W, P, RT):
 
 
 @pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("W", [8, 16, 32])
+@pytest.mark.parametrize("W", [8, 16, 28, 32])
 @pytest.mark.parametrize("P", [1, 2, 4])
 def test_fast_path_plans(gpu, W, P, RT):
     # queries long enough that most chunks take the fast path; lengths of every residue mod 4
@@ -193,7 +193,7 @@ def test_autotune_keeps_results(gpu):
     ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N)
     c0, e0 = ctx.forward(r, q)
     plan = ctx.autotune(r, q)
-    assert plan["tuned"] == 1 and plan["seg_width"] in (8, 16, 32)
+    assert plan["tuned"] == 1 and plan["seg_width"] in (8, 16, 20, 24, 28, 32)
     c1, e1 = ctx.forward(r, q)
     assert torch.equal(e0, e1)
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), c1.cpu().numpy(), e1.cpu().numpy()) == []
