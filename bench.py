@@ -38,12 +38,13 @@ LANES_PER_SM = 128        # 4 schedulers x 32 lanes
 L2_FLUSH_BYTES = 512 << 20
 
 # ncu DRAM traffic of one checkpointing forward launch on the paper batch, valid
-# only while the forward kernel source hashes to FWD_SRC_SHA (else reported as
-# null).  Captured on 128 of the 512 queries (2,341,632 bytes read + 1,553,270,784
-# written: the writes are the per-query checkpoints) and scaled by 4 to the
-# 512-query launch; profiles/fwd_chain_kernel_f32_ckpt_W24_RT4_paper_512x2000_vs_100000.md
-FWD_SRC_SHA = "1ccd745528cc5d57"
-FWD_TRAFFIC_BYTES = 4 * (2_341_632 + 1_553_270_784)
+# only while the forward kernel's code hashes to FWD_SRC_SHA (else reported as
+# null).  Captured on 128 of the 512 queries with the default plan (28 columns x
+# 4 rows per thread; 2,119,424 bytes read + 1,428,640,768 written: the writes
+# are the per-query checkpoints) and scaled by 4 to the 512-query launch;
+# profiles/fwd_chain_kernel_f32_ckpt_W28_RT4_paper_512x2000_vs_100000.md
+FWD_SRC_SHA = "3aad149b26285a44"
+FWD_TRAFFIC_BYTES = 4 * (2_119_424 + 1_428_640_768)
 
 
 def src_sha(path):
