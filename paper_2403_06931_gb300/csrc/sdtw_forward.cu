@@ -455,9 +455,13 @@ fwd_chain_kernel(const FwdArgs a)
                             // cell of the tile measured 17-21% of the whole fill
                             tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
                             if (p == lastt) bottom_min_prev<Md, W>(prev, B, base, M, best, best_col);
-                        } else {
+                        } else if (__any_sync(__activemask(), p == lastt)) {
+                            // the last row inside a tile: update the minimum in the cells,
+                            // only on the steps where some lane of the warp holds that tile
                             tile_step<Md, W, RT, true>(prev, A, y, x, diag, left, p == lastt ? bot : -1, B, base, M,
                                                        best, best_col);
+                        } else {
+                            tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
                         }
                         diag = left[RT - 1];
                         if (lane == 31) {
