@@ -230,12 +230,17 @@ sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t 
                                        int32_t* path, void* stream);
 
 /*
- * Time the candidate plans (segment width, warps per query, chain length) on
+ * Time the candidate plans (segment width, warps per query, tile height) on
  * the given device-resident batch and keep the fastest for calls of this
- * shape class (dtype, ragged or not, N and M buckets) on this context.
- * Runs several forwards on `stream` and synchronises it.  Arguments as
- * sdtw_forward; cost/end are scratch outputs.  *plan (if not NULL) receives
- * the chosen plan.  Errors: as sdtw_forward.
+ * shape class (dtype, ragged or not, N and M buckets, checkpoints) on this
+ * context.  On a context with SDTW_FLAG_KEEP_CHECKPOINTS whose workspace holds
+ * the batch's checkpoints, each candidate is timed as a forward with
+ * checkpoint stores followed by the backward (with zero upstream gradients
+ * into scratch it allocates for the call), so the plan serves the
+ * differentiable step.  Runs several forwards on `stream` and synchronises
+ * it.  Arguments as sdtw_forward; cost/end are scratch outputs.  *plan (if not
+ * NULL) receives the chosen plan.  Errors: as sdtw_forward, and SDTW_E_NOMEM
+ * when the backward's scratch cannot be allocated.
  */
 sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
                           const int64_t* offsets, int32_t B, int32_t N, void* cost,

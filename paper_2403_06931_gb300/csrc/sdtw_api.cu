@@ -136,11 +136,11 @@ sdtw_status ensure(sdtw_ctx* c, DevBuf& b, size_t bytes)
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
     // defaults measured on the paper's batch: 4 rows per thread, four warps
-    // per query, and 24 columns per thread for the plain fill, 28 with
-    // checkpoints (19.3 ms against 20.0, and a 6.3 ms backward against 6.7
-    // over its wider windows)
+    // per query, and 24 columns per thread for the plain fill, 32 with
+    // checkpoints (forward 16.5-16.7 ms and backward 5.8 ms over its wider
+    // windows: the fastest differentiable step)
     FwdPlan p;
-    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 28 : 24);
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : 24);
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
     p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
@@ -452,6 +452,45 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
     return run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, nullptr, 0, B);
 }
 
+// The backward of queries q0 .. q0+nq-1 from the checkpoints in ck written by
+// a forward with plan p: the band walk, then (with gradients) the reduction of
+// the reference gradient.  grad_queries == nullptr: the path only.
+cudaError_t launch_bwd(sdtw_ctx* ctx, const FwdPlan& p, const CkPtrs& ck, const float* ref, int64_t M,
+                       const float* queries, const int64_t* offsets, int32_t B, int32_t N, const int64_t* end,
+                       const float* grad_cost, float* grad_queries, float* grad_ref, int32_t* path, int q0, int nq,
+                       cudaStream_t st)
+{
+    sdtw::BwdArgs a{};
+    a.ref = ref;
+    a.M = M;
+    a.queries = queries;
+    a.offsets = offsets;
+    a.B = nq;
+    a.N = N;
+    a.q0 = q0;
+    a.B_total = B;
+    a.end = end;
+    a.grad_cost = grad_cost;
+    a.grad_queries = grad_queries;
+    a.path = path;
+    a.fr = ck.fr;
+    a.fr_slot = ck.fr_slot;
+    a.colck = ck.colck;
+    a.ck_slot = ck.ck_slot;
+    a.K = ck.K;
+    a.ck_cost = ck.ck_cost;
+    a.ck_end = ck.ck_end;
+    a.W = p.W;
+    a.P = p.P;
+    a.RT = p.RT;
+    a.gyq = ck.gyq;
+    a.span = ck.span;
+    a.status = ctx->d_status;
+    cudaError_t e = sdtw::launch_backward_walk(a, st);
+    if (e == cudaSuccess && grad_queries) e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st);
+    return e;
+}
+
 // The walk-back of every query from its end column, chunk by chunk of
 // queries; with grad_queries == nullptr only the path is written.
 static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
@@ -481,35 +520,8 @@ static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, cons
             s = run_forward(ctx, ref, M, queries, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, &p, &ck, q0, nq);
             if (s != SDTW_OK) return s;
         }
-        sdtw::BwdArgs a{};
-        a.ref = ref;
-        a.M = M;
-        a.queries = queries;
-        a.offsets = offsets;
-        a.B = nq;
-        a.N = N;
-        a.q0 = q0;
-        a.B_total = B;
-        a.end = end;
-        a.grad_cost = grad_cost;
-        a.grad_queries = grad_queries;
-        a.path = path;
-        a.fr = ck.fr;
-        a.fr_slot = ck.fr_slot;
-        a.colck = ck.colck;
-        a.ck_slot = ck.ck_slot;
-        a.K = ck.K;
-        a.ck_cost = ck.ck_cost;
-        a.ck_end = ck.ck_end;
-        a.W = p.W;
-        a.P = p.P;
-        a.RT = p.RT;
-        a.gyq = ck.gyq;
-        a.span = ck.span;
-        a.status = ctx->d_status;
-        if ((e = sdtw::launch_backward_walk(a, st)) != cudaSuccess) return cuda_fail(ctx, e);
-        if (grad_queries &&
-            (e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st)) != cudaSuccess)
+        if ((e = launch_bwd(ctx, p, ck, ref, M, queries, offsets, B, N, end, grad_cost, grad_queries, grad_ref, path,
+                            q0, nq, st)) != cudaSuccess)
             return cuda_fail(ctx, e);
     }
     if (!reuse) ctx->key.valid = false;
@@ -655,10 +667,31 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool ragged = offsets != nullptr;
     // with kept checkpoints, time the checkpointing forward (its stores
-    // included) among the plans whose checkpoints fit the arena
+    // included) and the backward that follows it, among the plans whose
+    // checkpoints fit the arena: the plan then serves the differentiable step
     const bool ckpt = keep_fits(ctx, B, N, M, ckpt_plan(ctx, B, N, M, ragged));
+    float *t_gc = nullptr, *t_gq = nullptr, *t_gr = nullptr;  // gradient scratch of the timed backward
+    auto free_scratch = [&]() {
+        cudaFree(t_gc);
+        cudaFree(t_gq);
+        cudaFree(t_gr);
+    };
+    if (ckpt && ctx->cfg.dtype == SDTW_F32) {
+        const size_t nqs = offsets ? static_cast<size_t>(ctx->cfg.max_total_query_len) : static_cast<size_t>(B) * N;
+        if (cudaMalloc(&t_gc, 4 * static_cast<size_t>(B)) != cudaSuccess ||
+            cudaMalloc(&t_gq, 4 * std::max<size_t>(nqs, 1)) != cudaSuccess ||
+            cudaMalloc(&t_gr, 4 * static_cast<size_t>(M)) != cudaSuccess ||
+            cudaMemsetAsync(t_gc, 0, 4 * static_cast<size_t>(B), st) != cudaSuccess) {
+            cudaGetLastError();
+            free_scratch();
+            return SDTW_E_NOMEM;
+        }
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SDTW_E_CUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        free_scratch();
+        return SDTW_E_CUDA;
+    }
     float best_ms = 1e30f;
     int best_w = 0, best_p = 0, best_rt = 0;
     const int Ws[] = {8, 16, 20, 24, 28, 32};
@@ -678,6 +711,9 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 const CkLayout l = ck_layout(M, N, p);
                 if (ckpt && B > chunk_capacity(ctx, l)) continue;
                 const CkPtrs ck = ckpt ? carve(ctx, l, B, M) : CkPtrs{};
+                const bool with_bwd = t_gc && sdtw::bwd_width_supported(W) &&
+                                      sdtw::bwd_smem_bytes(N, W, RT) <= kMaxSmem;
+                if (t_gc && !with_bwd) continue;  // a plan the backward cannot use
                 const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
                 if (per_sm <= 0) continue;
                 p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : B;
@@ -687,6 +723,10 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                     cudaEventRecord(e0, st);
                     s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &p, ckpt ? &ck : nullptr,
                                     0, B);
+                    if (s == SDTW_OK && with_bwd &&
+                        launch_bwd(ctx, p, ck, static_cast<const float*>(ref), M, static_cast<const float*>(queries),
+                                   offsets, B, N, end, t_gc, t_gq, t_gr, nullptr, 0, B, st) != cudaSuccess)
+                        s = SDTW_E_CUDA;
                     cudaEventRecord(e1, st);
                     if (s != SDTW_OK) break;
                     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -704,6 +744,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 if (s != SDTW_OK) {
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
+                    free_scratch();
                     return s;
                 }
                 if (ms < best_ms) {
@@ -717,6 +758,8 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    free_scratch();
     if (best_w == 0) return SDTW_E_UNSUPPORTED;
     ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] =
         std::make_tuple(best_w, best_p, best_rt);
