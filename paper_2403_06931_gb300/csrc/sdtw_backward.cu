@@ -19,14 +19,18 @@
 //   * the warp recomputes the band's rows down to the current cell from the
 //     chunk's wavefront and the window's boundary column, with the forward's
 //     own operations in the forward's own bases (four lanes per strip, W/4
-//     columns each, lane l one row behind lane l-1), so every value is the
+//     columns each; each step a lane advances RS rows, RS dependency chains,
+//     one step behind lane l-1), so every value is the
 //     forward's bit for bit; each cell's walk-back choice (two bits) is read
 //     off the minimum by equality (diagonal first, then left, then up -- the
 //     tie order of the walk-back);
 //   * the walk itself is cooperative: the 32 lanes read 32 cells of the
 //     current row at once and a ballot finds where the path leaves the row,
-//     so a horizontal run of the path costs one step per 32 cells; the row's
-//     gradient is a warp sum and finished columns are written in parallel.
+//     so a horizontal run of the path costs one step per 32 cells; finished
+//     columns are written in parallel, and each lane keeps its share of the
+//     current row's gradient, to be summed over lanes (in lane order) for all
+//     the band's rows at once when the walk leaves the band -- a sum per row
+//     on the walk's own chain of dependent steps would stall it.
 // At the first band the recomputed end cell must equal the forward's cost
 // exactly; a mismatch sets a status bit.
 //
@@ -60,20 +64,63 @@ struct DirWord<8> { using T = uint16_t; };
 
 constexpr int kDiag = 0, kLeft = 1, kUp = 2, kOutside = 3;
 
-__device__ __forceinline__ float warp_sum(float v)
+// Rows a lane advances per step of the band recompute, for bands of tiles of
+// RT rows: more rows give the lane more independent dependency chains, but
+// lengthen the 32-step fill and drain of the lane chain.
+constexpr int rows_per_step(int) { return 2; }
+
+// One lane's step of the band recompute: RS consecutive rows over the lane's
+// WB columns (D: the row above on entry, l: each row's left input, dg: the
+// diagonal of the first row), recording each cell's walk-back choice as two
+// bit masks per row.  Cells of row h depend on row h-1 in the same column and
+// on row h in the column to the left: RS dependency chains, each one column
+// behind the one above.  On exit D holds row RS-1, or with EXACT the last of
+// the v valid rows (rows at or below the band's end are computed from
+// placeholder inputs and never read), and l[h] holds row h's last column.
+template <int WB, int RS, bool EXACT>
+__device__ __forceinline__ void tile_rows(float (&D)[WB], const float (&y)[WB], const float (&x)[RS], float (&l)[RS],
+                                          float dg, int v, uint32_t (&nd)[RS], uint32_t (&nu)[RS])
 {
+    float dgs[RS];
+    dgs[0] = dg;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
+    for (int h = 1; h < RS; ++h) dgs[h] = l[h - 1];
+#pragma unroll
+    for (int h = 0; h < RS; ++h) nd[h] = nu[h] = 0u;
+#pragma unroll
+    for (int k = 0; k < WB; ++k) {
+        float up = D[k];
+        float row_v = up;
+#pragma unroll
+        for (int h = 0; h < RS; ++h) {
+            // bit k of nd: the minimum is not the diagonal; of nu: neither the
+            // diagonal nor the left cell (the cell above).  Written as selects:
+            // branches here stall a warp that runs alone on its scheduler.
+            const float m = min3_f32(up, dgs[h], l[h]);
+            const bool not_diag = m != dgs[h];
+            const bool is_up = not_diag & (m != l[h]);
+            nd[h] |= not_diag ? (1u << k) : 0u;
+            nu[h] |= is_up ? (1u << k) : 0u;
+            const float t = x[h] - y[k];
+            const float nv = fmaf(t, t, m);
+            dgs[h] = up;
+            l[h] = nv;
+            up = nv;
+            if constexpr (EXACT) {
+                if (h < v) row_v = nv;
+            }
+        }
+        D[k] = EXACT ? row_v : up;
+    }
 }
 
-template <int WB>
+template <int WB, int RT, int RS>
 __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
 {
+    static_assert(RT % RS == 0, "a step's rows lie in one tile");
     using DW = typename DirWord<WB>::T;
     constexpr int W = 4 * WB;    // forward segment width: four lanes per strip
     constexpr int KW = 32 * WB;  // window width K = 8 W
-    const int RT = a.RT;
     const int L = 32 * a.P;
     const int S = L * W;
     const int lane = threadIdx.x;
@@ -87,7 +134,9 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     float* xs = reinterpret_cast<float*>(smem_raw);  // [N] query samples
     float* ys = xs + N;                              // [KW] reference samples of the window
     float* lcol = ys + KW;                           // [RT*kChunk] the window's boundary column
-    DW* dirs = reinterpret_cast<DW*>(lcol + RT * kChunk);  // [2*steps][32] walk-back choices (two masks)
+    float* gqs = lcol + RT * kChunk;                 // [N] the query's gradient, summed band by band
+    float* rowpart = gqs + N;                        // [band rows][33] per-lane shares of each row's gradient
+    DW* dirs = reinterpret_cast<DW*>(rowpart + (RT * kChunk + 7 * RT) * 33);  // [RS*steps][32] walk-back choices
 
     int64_t start;
     int n;
@@ -127,7 +176,10 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     const bool grads = a.grad_queries != nullptr;  // false: the path only
     const float g2 = grads ? 2.f * a.grad_cost[q] : 0.f;
     const float* x = a.queries + start;
-    for (int i = lane; i < n; i += 32) xs[i] = x[i];
+    for (int i = lane; i < n; i += 32) {
+        xs[i] = x[i];
+        gqs[i] = 0.f;
+    }
     float* gyq = a.gyq + static_cast<int64_t>(ql) * a.M;
     float* gq = grads ? a.grad_queries + start : nullptr;
     int32_t* path = a.path ? a.path + 2 * start : nullptr;
@@ -143,7 +195,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     // walk state, identical in every lane: current cell (wi, wj), the
     // gradient of row wi and of column wj accumulated so far
     int wi = n - 1, wj = static_cast<int>(e64);
-    float ax = 0.f, ay = 0.f;
+    float axl = 0.f, ay = 0.f;  // this lane's share of row wi's gradient; column wj's so far
     bool done = false, first = true;
     if (lane == 0 && path) path[2 * wi + 1] = wj;
 
@@ -160,7 +212,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         const int dj = (wj - c0) / W;
         const int c = (wi / RT + lag0 + dj + s * Pp) / kChunk;
         const int ps0 = c * kChunk - lag0 - s * Pp;  // strip 0's tile at the chunk start
-        const int rtop = RT * (ps0 - 7);             // lane l handles row r at step r - rtop + l
+        const int rtop = RT * (ps0 - 7);             // the top of the band's rightmost strip
         const int ps = ps0 - d;                      // this lane's strip
         const int rf = RT * max(0, ps);              // its rows in the band: [rf, re)
         const int re = min(n, RT * min(nt, ps + kChunk));
@@ -210,20 +262,17 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         }
         // the first lane of strips 1..7: the left strip's last tile before the
         // band (rows RT*ps .. RT*ps + RT-1, its right-hand cells) and its base
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, dd = 0.f;
+        float e[RT], dd = 0.f;
+#pragma unroll
+        for (int h = 0; h < RT; ++h) e[h] = 0.f;
         if (sub == 0 && d >= 1) {
             float Bsrc = 0.f;
             if (ps + 1 >= 1 && ps + 1 <= nt) {
                 float dl;
                 rebase(tau - 1, Bsrc, dl);
-                e0 = rec_at(0, tau - 1) - dl;
-                if (RT == 2) {
-                    e1 = fr_at(W - 1, tau - 1) - dl;
-                } else {
-                    e1 = rec_at(1, tau - 1) - dl;
-                    e2 = rec_at(2, tau - 1) - dl;
-                    e3 = fr_at(W - 1, tau - 1) - dl;
-                }
+#pragma unroll
+                for (int h = 0; h < RT - 1; ++h) e[h] = rec_at(h, tau - 1) - dl;
+                e[RT - 1] = fr_at(W - 1, tau - 1) - dl;
             }
             dd = Bsrc - Bl;
         }
@@ -232,71 +281,56 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         for (int k = 0; k < WB; ++k) y[k] = ys[lane * WB + k];
 
         // ---- recompute the band's rows down to row wi, recording choices.
-        // Lane l handles rows r and r+1 (r - rtop even) at step (r - rtop)/2 + l:
-        // the two rows are two dependency chains, row r+1 one column behind.
-        const int steps = (wi - rtop) / 2 + 32;
+        // Lane l handles rows r .. r+RS-1 (r - rtop a multiple of RS, inside
+        // one tile) at step (r - rtop)/RS + l.  A lane's last step in the band
+        // may reach past row hi-1: those rows take a left input of +inf (or
+        // the left lane's equally invalid rows) and a sample of 0, and are
+        // never read -- the walk reads rows up to wi, and a strip's right
+        // neighbour ends its band no lower.
+        const int steps = (wi - rtop) / RS + 32;
         const int hi = min(re, wi + 1);  // this lane's rows end here
-        float lastA = 0.f, lastB = 0.f;  // right-hand cells of the lane's previous row pair
-        for (int sg = 0; sg < steps; ++sg) {
-            const float recvA = __shfl_up_sync(0xffffffffu, lastA, 1);
-            const float recvB = __shfl_up_sync(0xffffffffu, lastB, 1);
-            const int r = rtop + 2 * (sg - lane);
-            if (r >= rf && r < hi) {
-                const bool vb = r + 1 < hi;  // row r+1 is in the band (else: last row)
-                float lA, lB;
-                if (sub != 0) {
-                    lA = recvA;  // same strip, same base
-                    lB = recvB;
-                } else if (d == 0) {
-                    lA = b == 0 ? INF : lcol[r - rf0];  // already in this strip's base
-                    lB = (b == 0 || !vb) ? INF : lcol[r + 1 - rf0];
-                } else {
-                    float vA = recvA, vB = recvB;
-                    if (r < rf_left) {
-                        // the left strip's last tile before the band (rows RT*ps ..)
-                        const int e = r - RT * ps;
-                        vA = e == 0 ? e0 : e2;
-                        vB = e == 0 ? e1 : e3;
-                    }
-                    lA = vA + dd;  // into this strip's base, as the forward converts
-                    lB = vB + dd;
-                }
-                const float xA = xs[r];
-                const float xB = vb ? xs[r + 1] : 0.f;
-                const float convA = lA, convB = lB;
-                float dgA = dg, dgB = lA;
-                // walk-back choices as two masks per row: bit k of nd is set
-                // unless the minimum is the diagonal; bit k of nu is set when it
-                // is neither the diagonal nor the left cell (the cell above)
-                uint32_t ndA = 0, nuA = 0, ndB = 0, nuB = 0;
+        float last[RS];                  // right-hand cells of the lane's previous rows
 #pragma unroll
-                for (int k = 0; k < WB; ++k) {
-                    const float up = D[k];
-                    const float vA = min3_f32(up, dgA, lA);
-                    if (vA != dgA) {
-                        ndA |= 1u << k;
-                        if (vA != lA) nuA |= 1u << k;
-                    }
-                    const float tA = xA - y[k];
-                    const float nA = fmaf(tA, tA, vA);
-                    dgA = up;
-                    lA = nA;
-                    const float vB = min3_f32(nA, dgB, lB);
-                    if (vB != dgB) {
-                        ndB |= 1u << k;
-                        if (vB != lB) nuB |= 1u << k;
-                    }
-                    const float tB = xB - y[k];
-                    const float nB = fmaf(tB, tB, vB);
-                    dgB = nA;
-                    lB = nB;
-                    D[k] = vb ? nB : nA;
+        for (int h = 0; h < RS; ++h) last[h] = 0.f;
+        for (int sg = 0; sg < steps; ++sg) {
+            float recv[RS];
+#pragma unroll
+            for (int h = 0; h < RS; ++h) recv[h] = __shfl_up_sync(0xffffffffu, last[h], 1);
+            const int r = rtop + RS * (sg - lane);
+            if (r >= rf && r < hi) {
+                const int v = min(RS, hi - r);  // valid rows of this step
+                // left inputs without divergent branches: a strip's first lane
+                // converts its left strip's values (from the left lane, or the
+                // stored record for the strip's first tile) into its own base
+                // (dd is 0 for the other lanes, whose values share the base), the
+                // window's first strip reads the stored boundary column
+                const bool from_rec = sub == 0 && r < rf_left;  // a strip's first tile, first lane
+                const int eo = r - rf;                           // ... and the step's rows in it
+                float l[RS], x[RS];
+#pragma unroll
+                for (int h = 0; h < RS; ++h) {
+                    float ev = e[h];
+#pragma unroll
+                    for (int o = RS; o < RT; o += RS)
+                        if (eo == o) ev = e[h + o];
+                    float lv = (from_rec ? ev : recv[h]) + dd;
+                    if (d == 0 && sub == 0) lv = INF;
+                    if (d == 0 && sub == 0 && b > 0 && h < v) lv = lcol[r + h - rf0];
+                    l[h] = lv;
+                    x[h] = h < v ? xs[r + h] : 0.f;
                 }
-                lastA = lA;
-                lastB = lB;
-                dg = vb ? convB : convA;
-                dirs[(2 * sg) * 32 + lane] = static_cast<DW>(ndA | (nuA << WB));
-                dirs[(2 * sg + 1) * 32 + lane] = static_cast<DW>(ndB | (nuB << WB));
+                const float dg_next = l[RS - 1];
+                uint32_t nd[RS], nu[RS];
+                if (first)
+                    tile_rows<WB, RS, true>(D, y, x, l, dg, v, nd, nu);
+                else
+                    tile_rows<WB, RS, false>(D, y, x, l, dg, v, nd, nu);
+#pragma unroll
+                for (int h = 0; h < RS; ++h) {
+                    last[h] = l[h];
+                    dirs[(RS * sg + h) * 32 + lane] = static_cast<DW>(nd[h] | (nu[h] << WB));
+                }
+                dg = dg_next;
             }
         }
 
@@ -315,20 +349,22 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         __syncwarp();
 
         // ---- follow the path through the band, 32 cells of a row at a time
+        const int wtop = wi;  // the band's rows the walk visits: [wlo, wtop]
+        int wlo = wi;
         for (;;) {
             const float xi = xs[wi];
             if (wi == 0) {
                 // the path starts here: only this cell of row 0 is on it
                 const float cg = g2 * (xi - ys[wj - c0]);
                 if (lane == 0) {
-                    if (grads) {
-                        gq[0] = ax + cg;
-                        gyq[wj] = ay - cg;
-                    }
+                    axl += cg;
+                    if (grads) gyq[wj] = ay - cg;
                     if (path) path[0] = wj;
                     a.span[2 * ql] = wj;
                     a.span[2 * ql + 1] = e64;
                 }
+                rowpart[(wi - rtop) * 33 + lane] = axl;
+                wlo = 0;
                 done = true;
                 break;
             }
@@ -340,7 +376,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
                     if (jk == 0) {
                         code = kUp;
                     } else {
-                        const uint32_t m = dirs[(wi - rtop + 2 * lam) * 32 + lam] >> (cc - lam * WB);
+                        const uint32_t m = dirs[(wi - rtop + RS * lam) * 32 + lam] >> (cc - lam * WB);
                         code = !(m & 1u) ? kDiag : ((m >> WB) & 1u) ? kUp : kLeft;
                     }
                 }
@@ -351,7 +387,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
             const int last = fcode == kOutside ? f - 1 : (f < 32 ? f : 31);  // last lane on the path
             const bool on = lane <= last;
             const float cg = on ? g2 * (xi - ys[jk - c0]) : 0.f;
-            ax += warp_sum(cg);
+            axl += cg;
             // column of lane k: finished unless the path goes up from it
             float vy = -cg;
             if (lane == 0) vy += ay;
@@ -359,23 +395,47 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
             if (grads && on && lcode != kUp) gyq[jk] = vy;
             const float vlast = __shfl_sync(0xffffffffu, vy, last);
             ay = (f < 32 && fcode == kUp) ? vlast : 0.f;
-            if (f < 32 && fcode != kOutside) {
+            const bool row_ends = f < 32 && fcode != kOutside;
+            if (row_ends) {
                 // the row ends at (wi, wj - last); move up or diagonally
                 const int jl = wj - last;
-                if (lane == 0) {
-                    if (grads) gq[wi] = ax;
-                    if (path) path[2 * wi] = jl;
-                }
-                ax = 0.f;
+                rowpart[(wi - rtop) * 33 + lane] = axl;
+                axl = 0.f;
+                wlo = wi;
+                if (lane == 0 && path) path[2 * wi] = jl;
                 wi -= 1;
                 wj = fcode == kDiag ? jl - 1 : jl;
                 if (lane == 0 && path) path[2 * wi + 1] = wj;
             } else {
                 wj -= last + 1;  // the run continues to the left
             }
-            if (wj < c0 || wi < RT * max(0, ps0 - (wj - c0) / W)) break;  // left the band
+            if (wj < c0 || wi < RT * max(0, ps0 - (wj - c0) / W)) {
+                // left the band; a row left unfinished continues in the next band
+                if (!row_ends) {
+                    rowpart[(wi - rtop) * 33 + lane] = axl;
+                    axl = 0.f;
+                    wlo = wi;
+                }
+                break;
+            }
         }
+        // the rows' gradients: each lane sums rows of the band over the 32
+        // shares in lane order and adds them to the query's gradient (the rows
+        // are 33 floats apart, so the lanes read distinct banks)
+        __syncwarp();
+        if (grads) {
+            for (int i = wlo + lane; i <= wtop; i += 32) {
+                const float* rp = rowpart + (i - rtop) * 33;
+                float sum = 0.f;
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum += rp[k];
+                gqs[i] += sum;
+            }
+        }
+        __syncwarp();
     }
+    if (grads)
+        for (int i = lane; i < n; i += 32) gq[i] = gqs[i];
 }
 
 // grad_ref[j] (+)= sum over queries q (in order) whose path spans column j of gyq[q][j]
@@ -396,7 +456,7 @@ template <int WB>
 cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 {
     const int smem = bwd_smem_bytes(a.N, 4 * WB, a.RT);
-    auto k = bwd_band_kernel<WB>;
+    auto k = a.RT == 2 ? bwd_band_kernel<WB, 2, rows_per_step(2)> : bwd_band_kernel<WB, 4, rows_per_step(4)>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -411,10 +471,15 @@ bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 20 || W == 24
 
 int bwd_smem_bytes(int N, int W, int RT)
 {
-    // query samples, the window's samples and boundary column, and the
-    // choices of up to RT*kChunk + 7*RT + 64 rows of 32 lanes (W/2 bits each)
+    // query samples and gradient, the window's samples and boundary column,
+    // the lanes' shares of the band's row gradients (33 floats per row), and
+    // the choices of up to RT*kChunk + 7*RT + 32*RS rows of 32 lanes (W/2 bits
+    // each): the band's rows below the top of its rightmost strip, and the
+    // lag of RS rows per lane
     const int word = W <= 16 ? 1 : 2;
-    return 4 * (N + 8 * W + RT * kChunk) + (RT * kChunk + 7 * RT + 64) * 32 * word;
+    const int RS = rows_per_step(RT);
+    return 4 * (2 * N + 8 * W + RT * kChunk) + 4 * (RT * kChunk + 7 * RT) * 33 +
+           (RT * kChunk + 7 * RT + 32 * RS) * 32 * word;
 }
 
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)

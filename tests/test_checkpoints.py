@@ -340,7 +340,8 @@ def test_walk_through_bands_matches_full_matrix(P, W, RT, n, M):
 # ---------------------------------------------------------------------------
 # The backward kernel's own schedule (csrc/sdtw_backward.cu bwd_band_kernel),
 # transliterated: the flat checkpoint layouts the forward writes, the warp's
-# 32 lanes (four per strip, W/4 columns each, lane l one row behind lane l-1),
+# 32 lanes (four per strip, W/4 columns each, one tile of rows per step, lane l
+# one step behind lane l-1),
 # the per-lane band bounds, and the cooperative walk with its band exits.
 
 def flat_checkpoints(fw, pl):
@@ -364,9 +365,15 @@ def flat_checkpoints(fw, pl):
     return fr, ck
 
 
-def kernel_backward(fw, pl, end):
-    """The warp's walk from (n-1, end): (cells of the path, recomputed D at the
-    end cell, number of bands)."""
+def rows_per_step(RT):
+    """Rows a lane advances per step (csrc/sdtw_backward.cu rows_per_step)."""
+    return 2
+
+
+def kernel_backward(fw, pl, end, RS=None):
+    """The warp's walk from (n-1, end) with RS rows per lane step: (cells of
+    the path, recomputed D at the end cell, number of bands)."""
+    RS = rows_per_step(pl.RT) if RS is None else RS
     n, M, W, RT, L, S, Pp, nt = pl.n, pl.M, pl.W, pl.RT, pl.L, pl.S, pl.Pp, pl.nt
     WB, KW, KC = W // 4, 32 * (W // 4), K_CHUNK
     E = 4 if RT == 2 else 8
@@ -421,47 +428,52 @@ def kernel_backward(fw, pl, end):
                 st["dd"] = r32(bsrc - st["B"])
             st["y"] = ys[lane * WB:(lane + 1) * WB]
             lanes.append(st)
-        # lane l handles rows r, r+1 (r - rtop even) at step (r - rtop) / 2 + l
-        steps = (wi - rtop) // 2 + 32
+        # lane l handles rows r .. r+RS-1 (r - rtop a multiple of RS, inside one
+        # tile) at step (r - rtop) / RS + l; rows at or below its band end are
+        # computed too (from a left input of +inf, or the neighbour's equally
+        # invalid rows, and a query sample of 0) but never read.  After each
+        # step D holds the step's last row, except in the first band, where it
+        # holds the last valid row (the end cell's row) for the check below.
+        steps = (wi - rtop) // RS + 32
         dirs = {}
         for st in lanes:
-            st["last"] = [0.0, 0.0]
+            st["last"] = [0.0] * RS
         for sg in range(steps):
             recv = [lanes[max(0, lane - 1)]["last"][:] for lane in range(32)]
             for lane, st in enumerate(lanes):
-                r = rtop + 2 * (sg - lane)
+                r = rtop + RS * (sg - lane)
                 hi = min(st["re"], wi + 1)
                 if not (st["rf"] <= r < hi):
                     continue
-                vb = r + 1 < hi
+                v = min(RS, hi - r)            # valid rows of this step
                 lefts = []
-                for h in range(2):
+                for h in range(RS):
                     rr = r + h
-                    if h == 1 and not vb:
-                        lefts.append(INF)
-                    elif st["sub"] != 0:
+                    if st["sub"] != 0:
                         lefts.append(recv[lane][h])
                     elif st["d"] == 0:
-                        lefts.append(INF if b == 0 else lcol[rr - rf0])
+                        lefts.append(INF if (b == 0 or h >= v) else lcol[rr - rf0])
                     else:
-                        v = recv[lane][h] if r >= st["rf_left"] else st["e"][rr - RT * st["ps"]]
-                        lefts.append(r32(v + st["dd"]))
-                lA, lB = lefts
-                dgA, dgB = st["dg"], lA
-                cA, cB = [], []
+                        src = recv[lane][h] if r >= st["rf_left"] else st["e"][rr - RT * st["ps"]]
+                        lefts.append(r32(src + st["dd"]))
+                xv = [xs[r + h] if h < v else 0.0 for h in range(RS)]
+                ls = lefts[:]
+                dgs = [st["dg"]] + lefts[:-1]  # row h's diagonal at the strip's first column
+                codes = [[] for _ in range(RS)]
                 for k in range(WB):
                     up = st["D"][k]
-                    nA, ca = cell(xs[r], st["y"][k], up, dgA, lA)
-                    dgA, lA = up, nA
-                    nB, cb = cell(xs[r + 1], st["y"][k], nA, dgB, lB)
-                    dgB, lB = nA, nB
-                    cA.append(ca)
-                    cB.append(cb)
-                    st["D"][k] = nB if vb else nA
-                st["last"] = [dgB, lB]           # row r's and row r+1's last column
-                st["dg"] = lefts[1] if vb else lefts[0]
-                dirs[(2 * sg, lane)] = cA
-                dirs[(2 * sg + 1, lane)] = cB
+                    rows = []
+                    for h in range(RS):
+                        nv, cd = cell(xv[h], st["y"][k], up, dgs[h], ls[h])
+                        codes[h].append(cd)
+                        dgs[h], ls[h] = up, nv
+                        up = nv
+                        rows.append(nv)
+                    st["D"][k] = rows[v - 1] if first else rows[RS - 1]
+                st["last"] = ls[:]
+                st["dg"] = lefts[RS - 1]
+                for h in range(RS):
+                    dirs[(RS * sg + h, lane)] = codes[h]
         if first:
             lj, kj = (wj - c0) // WB, (wj - c0) % WB
             v_end = r32(lanes[lj]["D"][kj] + lanes[lj]["B"])
@@ -479,7 +491,7 @@ def kernel_backward(fw, pl, end):
                     cc = jk - c0
                     lam = cc // WB
                     if wi >= RT * max(0, ps0 - (lam >> 2)):
-                        code = UP if jk == 0 else dirs[(wi - rtop + 2 * lam, lam)][cc - lam * WB]
+                        code = UP if jk == 0 else dirs[(wi - rtop + RS * lam, lam)][cc - lam * WB]
                 codes.append(code)
             f = next((k for k in range(32) if codes[k] != LEFT), 32)
             fcode = codes[f] if f < 32 else LEFT
@@ -508,13 +520,18 @@ KERNEL_CASES = [
     (1, 8, 2, 70, 900),
     (1, 4, 4, 299, 500),
     (2, 8, 4, 97, 1300),
+    (1, 8, 4, 150, 800),    # the last tile holds two of the query's rows
 ]
 
 
+@pytest.mark.parametrize("two_rows", [False, True])
 @pytest.mark.parametrize("P,W,RT,n,M", KERNEL_CASES)
-def test_kernel_band_schedule_and_walk(P, W, RT, n, M):
+def test_kernel_band_schedule_and_walk(P, W, RT, n, M, two_rows):
+    """Both step heights a band of 4-row tiles can take (2 rows or the tile)."""
+    if two_rows and RT == 2:
+        pytest.skip("2-row tiles take 2-row steps")
     pl, fw = _setup(P, W, RT, n, M, seed=n * 13 + M)
-    cells, v_end, bands = kernel_backward(fw, pl, fw["end"])
+    cells, v_end, bands = kernel_backward(fw, pl, fw["end"], RS=2 if two_rows else RT)
     assert v_end == fw["cost"]
     full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
     assert cells == full
