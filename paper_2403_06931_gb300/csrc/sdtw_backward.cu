@@ -287,12 +287,19 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         // the left lane's equally invalid rows) and a sample of 0, and are
         // never read -- the walk reads rows up to wi, and a strip's right
         // neighbour ends its band no lower.
-        const int steps = (wi - rtop) / RS + 32;
+        // the walk moves up and left from (wi, wj): strips right of wj's strip dj
+        // are not needed, so the schedule ends when strip dj's last lane has
+        // computed row wi
+        const int steps = (wi - rtop) / RS + 4 * dj + 4;
         const int hi = min(re, wi + 1);  // this lane's rows end here
         float last[RS];                  // right-hand cells of the lane's previous rows
 #pragma unroll
         for (int h = 0; h < RS; ++h) last[h] = 0.f;
-        for (int sg = 0; sg < steps; ++sg) {
+        // no lane has rows before its first step in the band: start at the
+        // earliest of those (the rightmost strip's top is up to 7 tiles above
+        // the others', so the first steps are often empty)
+        const int sg0 = __reduce_min_sync(0xffffffffu, static_cast<unsigned>(rf < hi ? (rf - rtop) / RS + lane : steps));
+        for (int sg = sg0; sg < steps; ++sg) {
             float recv[RS];
 #pragma unroll
             for (int h = 0; h < RS; ++h) recv[h] = __shfl_up_sync(0xffffffffu, last[h], 1);

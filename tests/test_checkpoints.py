@@ -434,11 +434,14 @@ def kernel_backward(fw, pl, end, RS=None):
         # invalid rows, and a query sample of 0) but never read.  After each
         # step D holds the step's last row, except in the first band, where it
         # holds the last valid row (the end cell's row) for the check below.
-        steps = (wi - rtop) // RS + 32
+        steps = (wi - rtop) // RS + 4 * dj + 4   # strips right of wj's are not needed
         dirs = {}
         for st in lanes:
             st["last"] = [0.0] * RS
-        for sg in range(steps):
+        # the kernel starts at the earliest step at which some lane has rows
+        sg0 = min((st["rf"] - rtop) // RS + lane if st["rf"] < min(st["re"], wi + 1) else steps
+                  for lane, st in enumerate(lanes))
+        for sg in range(sg0, steps):
             recv = [lanes[max(0, lane - 1)]["last"][:] for lane in range(32)]
             for lane, st in enumerate(lanes):
                 r = rtop + RS * (sg - lane)
