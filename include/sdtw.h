@@ -33,7 +33,8 @@
  *     left unwritten.
  *   - A context is not thread-safe: use one context per host thread / stream.
  *   - Inputs must be finite.  Inputs are used as given; z-normalisation (the
- *     paper's Eq. 2) is the caller's step.
+ *     paper's Eq. 2) is the caller's step (sdtw_znormalize), or the
+ *     library's for the queries with SDTW_FLAG_ZNORM_QUERIES.
  */
 #ifndef SDTW_H
 #define SDTW_H
@@ -67,6 +68,17 @@ typedef enum sdtw_dtype {
 #define SDTW_FLAG_GRAD 0x1u             /* the context will run sdtw_backward: size checkpoint workspace */
 #define SDTW_FLAG_KEEP_CHECKPOINTS 0x2u /* sdtw_forward also stores the checkpoints sdtw_backward needs */
 #define SDTW_FLAG_NO_AUTOTUNE 0x4u      /* use the built-in default plan instead of timing candidates */
+/* SDTW_F32 only: sdtw_forward, sdtw_backward, sdtw_path and sdtw_autotune
+ * z-normalise every query (paper Eq. 2, bit for bit as sdtw_znormalize does on
+ * 16-byte-aligned buffers)
+ * into a device copy the context owns before the fill, so the caller passes
+ * raw queries; sdtw_backward's grad_queries is then the gradient with respect
+ * to the raw queries (the normalisation's own derivative applied on the
+ * device).  The reference is used as given (normalise it once with
+ * sdtw_znormalize).  The copy holds max_total_query_len floats; a ragged
+ * query that would reach past it is skipped and reported like a query longer
+ * than N. */
+#define SDTW_FLAG_ZNORM_QUERIES 0x8u
 
 typedef struct sdtw_config {
     sdtw_dtype dtype;

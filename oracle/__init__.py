@@ -114,6 +114,26 @@ def znormalize(x):
     return out
 
 
+def znormalize_vjp(x, gz):
+    """The derivative of Eq. 2 applied to a gradient, in float64.
+
+    For z = (x - mean) / S with the population spread S (S == 0: z = x - mean),
+    and g = d cost / d z, returns d cost / d x.  Differentiating mean = sum(x)/n
+    and S = sqrt(sum((x - mean)^2) / n) gives d z_i / d x_k =
+    (delta_ik - 1/n - z_i z_k / n) / S, hence
+    d cost / d x_k = (g_k - mean(g) - z_k mean(g z)) / S; with S == 0 the
+    series is only centred and the result is g - mean(g)."""
+    xv = np.asarray(x, dtype=np.float64)
+    g = np.asarray(gz, dtype=np.float64)
+    n = xv.shape[0]
+    mu = xv.sum() / n
+    c = xv - mu
+    var = (c * c).sum() / n
+    inv = 1.0 / np.sqrt(var) if var > 0 else 1.0
+    z = c * inv
+    return inv * (g - g.mean() - z * (g * z).mean())
+
+
 def znormalize_batch(values, offsets=None, N=None):
     """znormalize every series of a batch stored back to back ([B][N] or by offsets)."""
     v = np.asarray(values, dtype=np.float64).reshape(-1)

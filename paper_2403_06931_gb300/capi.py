@@ -29,6 +29,7 @@ SDTW_I8 = 1
 SDTW_FLAG_GRAD = 0x1
 SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
+SDTW_FLAG_ZNORM_QUERIES = 0x8
 
 ABI_VERSION = 3
 

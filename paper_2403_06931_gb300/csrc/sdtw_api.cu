@@ -84,6 +84,9 @@ struct sdtw_ctx {
     // host-call staging
     DevBuf st_ref, st_q, st_off, st_cost, st_end, st_gc, st_gq, st_gr, st_path;
 
+    // SDTW_FLAG_ZNORM_QUERIES: the z-normalised queries (max_total_query_len floats)
+    float* d_zq = nullptr;
+
     std::map<TuneKey, std::tuple<int, int, int>> tuned;  // -> (W, P, RT)
 };
 
@@ -265,6 +268,8 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
         a.K = 1;
     }
     a.status = c->d_status;
+    // the context's normalised copy holds max_total_query_len samples
+    a.q_limit = (c->cfg.flags & SDTW_FLAG_ZNORM_QUERIES) ? c->cfg.max_total_query_len : 0;
     a.queue = nullptr;
     a.order = nullptr;
     cudaError_t e;
@@ -311,9 +316,24 @@ void free_all(sdtw_ctx* c)
     dev_free(c, c->d_arena, 4 * c->arena_floats);
     dev_free(c, c->d_cost_tmp, 4 * static_cast<size_t>(c->cfg.max_batch));
     dev_free(c, c->d_end_tmp, 8 * static_cast<size_t>(c->cfg.max_batch));
+    dev_free(c, c->d_zq, 4 * static_cast<size_t>(c->cfg.max_total_query_len));
     for (DevBuf* b : {&c->st_ref, &c->st_q, &c->st_off, &c->st_cost, &c->st_end, &c->st_gc, &c->st_gq, &c->st_gr,
                       &c->st_path})
         dev_free(c, b->p, b->bytes);
+}
+
+// The queries the fill reads: the caller's, or with SDTW_FLAG_ZNORM_QUERIES
+// their z-normalised copy in the context (written here, on the stream).
+sdtw_status fill_queries(sdtw_ctx* c, const void* queries, const int64_t* offsets, int32_t B, int32_t N, cudaStream_t st,
+                         const void** out)
+{
+    *out = queries;
+    if (!(c->cfg.flags & SDTW_FLAG_ZNORM_QUERIES) || B == 0) return SDTW_OK;
+    const cudaError_t e = sdtw::launch_znormalize(static_cast<const float*>(queries), c->d_zq, offsets, B, N,
+                                                  c->cfg.max_total_query_len, c->d_status, st);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    *out = c->d_zq;
+    return SDTW_OK;
 }
 
 bool key_matches(const CkptKey& k, const void* ref, int64_t M, const void* q, const int64_t* off, int32_t B,
@@ -376,6 +396,7 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if (cfg->max_ref_len > INT_MAX / 2) return SDTW_E_INVALID;
     if ((cfg->flags & (SDTW_FLAG_GRAD | SDTW_FLAG_KEEP_CHECKPOINTS)) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
+    if ((cfg->flags & SDTW_FLAG_ZNORM_QUERIES) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
     if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0) return SDTW_E_INVALID;
@@ -397,6 +418,8 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     sdtw_status s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
     if (s == SDTW_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_queue), sizeof(int));
     if (s == SDTW_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_order), 4 * static_cast<size_t>(cfg->max_batch));
+    if (s == SDTW_OK && (cfg->flags & SDTW_FLAG_ZNORM_QUERIES))
+        s = dev_alloc(c, reinterpret_cast<void**>(&c->d_zq), 4 * static_cast<size_t>(cfg->max_total_query_len));
     if (s == SDTW_OK && (cfg->flags & SDTW_FLAG_GRAD)) s = alloc_backward(c);
     if (s == SDTW_OK) {
         e = cudaMemset(c->d_status, 0, sizeof(int));
@@ -430,11 +453,13 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
     if (B == 0) return SDTW_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->key.valid = false;
+    const void* fq;
+    if ((s = fill_queries(ctx, queries, offsets, B, N, st, &fq)) != SDTW_OK) return s;
     const FwdPlan cp = ckpt_plan(ctx, B, N, M, offsets != nullptr);
     if (keep_fits(ctx, B, N, M, cp)) {
         // store the checkpoints a following sdtw_backward on these inputs reuses
         const CkPtrs ck = carve(ctx, ck_layout(M, N, cp), B, M);
-        s = run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, &cp, &ck, 0, B);
+        s = run_forward(ctx, ref, M, fq, offsets, B, N, cost, end, st, &cp, &ck, 0, B);
         if (s == SDTW_OK) {
             ctx->key.ref = ref;
             ctx->key.queries = queries;
@@ -449,7 +474,7 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
         }
         return s;
     }
-    return run_forward(ctx, ref, M, queries, offsets, B, N, cost, end, st, nullptr, nullptr, 0, B);
+    return run_forward(ctx, ref, M, fq, offsets, B, N, cost, end, st, nullptr, nullptr, 0, B);
 }
 
 // The backward of queries q0 .. q0+nq-1 from the checkpoints in ck written by
@@ -486,6 +511,7 @@ cudaError_t launch_bwd(sdtw_ctx* ctx, const FwdPlan& p, const CkPtrs& ck, const 
     a.gyq = ck.gyq;
     a.span = ck.span;
     a.status = ctx->d_status;
+    a.q_limit = (ctx->cfg.flags & SDTW_FLAG_ZNORM_QUERIES) ? ctx->cfg.max_total_query_len : 0;
     cudaError_t e = sdtw::launch_backward_walk(a, st);
     if (e == cudaSuccess && grad_queries) e = sdtw::launch_grad_ref_reduce(ck.gyq, ck.span, nq, M, q0 > 0, grad_ref, st);
     return e;
@@ -501,6 +527,9 @@ static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, cons
     cudaError_t e;
     // the plan of the checkpoints: the kept forward's, or the one re-run here
     const bool reuse = key_matches(ctx->key, ref, M, queries, offsets, B, N);
+    const void* fqv;
+    if ((s = fill_queries(ctx, queries, offsets, B, N, st, &fqv)) != SDTW_OK) return s;
+    const float* fq = static_cast<const float*>(fqv);
     FwdPlan p = ckpt_plan(ctx, B, N, M, offsets != nullptr);
     if (reuse) {
         p.W = ctx->key.W;
@@ -517,13 +546,18 @@ static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, cons
     for (int q0 = 0; q0 < B; q0 += chunk) {
         const int nq = std::min(chunk, B - q0);
         if (!reuse) {
-            s = run_forward(ctx, ref, M, queries, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, &p, &ck, q0, nq);
+            s = run_forward(ctx, ref, M, fq, offsets, B, N, ctx->d_cost_tmp, ctx->d_end_tmp, st, &p, &ck, q0, nq);
             if (s != SDTW_OK) return s;
         }
-        if ((e = launch_bwd(ctx, p, ck, ref, M, queries, offsets, B, N, end, grad_cost, grad_queries, grad_ref, path,
+        if ((e = launch_bwd(ctx, p, ck, ref, M, fq, offsets, B, N, end, grad_cost, grad_queries, grad_ref, path,
                             q0, nq, st)) != cudaSuccess)
             return cuda_fail(ctx, e);
     }
+    // with normalised queries: the gradient with respect to the raw ones
+    if (grad_queries && fq != queries &&
+        (e = sdtw::launch_znorm_vjp(queries, grad_queries, offsets, B, N, ctx->cfg.max_total_query_len, st)) !=
+            cudaSuccess)
+        return cuda_fail(ctx, e);
     if (!reuse) ctx->key.valid = false;
     return SDTW_OK;
 }
@@ -666,6 +700,8 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     if (B == 0) return SDTW_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool ragged = offsets != nullptr;
+    // every timed run reads the queries the fill would read
+    if ((s = fill_queries(ctx, queries, offsets, B, N, st, &queries)) != SDTW_OK) return s;
     // with kept checkpoints, time the checkpointing forward (its stores
     // included) and the backward that follows it, among the plans whose
     // checkpoints fit the arena: the plan then serves the differentiable step

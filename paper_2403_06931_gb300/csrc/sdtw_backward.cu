@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         start = a.offsets[q];
         const int64_t stop = a.offsets[q + 1];
         const int64_t len = stop - start;
-        if (start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total]) {
+        if (start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total] || (a.q_limit > 0 && stop > a.q_limit)) {
             if (lane == 0) {
                 atomicOr(a.status, kStatusBadLength);
                 a.span[2 * ql] = 0;

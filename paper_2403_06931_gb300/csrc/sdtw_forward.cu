@@ -261,7 +261,7 @@ fwd_chain_kernel(const FwdArgs a)
             start = a.offsets[q];
             const int64_t stop = a.offsets[q + 1];
             const int64_t len = stop - start;
-            bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total];
+            bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total] || (a.q_limit > 0 && stop > a.q_limit);
             if (bad) {
                 if (threadIdx.x == 0) atomicOr(a.status, kStatusBadLength);
                 __syncthreads();

@@ -62,6 +62,7 @@ struct FwdArgs {
     float* ck_cost;
     int64_t* ck_end;
     int* status;
+    int64_t q_limit;     // > 0: queries end within this many samples (a ragged query past it is flagged)
     int* queue;          // persistent mode: device work counter (reset to 0 before the launch)
     const int32_t* order;// persistent mode: query order (longest first), or nullptr
 };
@@ -110,6 +111,7 @@ struct BwdArgs {
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
     int64_t* span;   // [B][2] first and last column of each query's path
     int* status;
+    int64_t q_limit; // > 0: queries end within this many samples (a ragged query past it is flagged)
 };
 
 // Checkpoint geometry of a forward plan (sdtw_forward.cu): floats of one
@@ -127,5 +129,14 @@ int bwd_smem_bytes(int N, int W, int RT);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);
+
+// Batch z-normalisation (sdtw_norm.cu): Eq. 2 on B series ([B][N] or by
+// offsets) from `in` to `out`; a ragged series reaching past `limit` elements
+// (limit < 0: no bound) is skipped and reported in *status.  The derivative:
+// g (dcost/dz, same layout) becomes dcost/dx in place.
+cudaError_t launch_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N, int64_t limit,
+                              int* status, cudaStream_t st);
+cudaError_t launch_znorm_vjp(const float* x, float* g, const int64_t* offsets, int32_t B, int32_t N, int64_t limit,
+                             cudaStream_t st);
 
 }  // namespace sdtw

@@ -25,7 +25,7 @@
 
 #include <cstdint>
 
-#include "sdtw.h"
+#include "sdtw_internal.h"
 
 namespace {
 
@@ -126,22 +126,76 @@ __device__ __forceinline__ void znorm_series(const float* x, float* z, int64_t n
     for (int64_t i = idx; i < n; i += count) z[i] = ((x[i] - mean.hi) - mean.lo) * inv;
 }
 
-// one CTA per series: long series, and ragged batches (lengths on the device)
-__global__ void __launch_bounds__(kNormThreads)
-znorm_kernel(const float* in, float* out, const int64_t* offsets, int32_t N)
+// The series q of a batch: [a, a + n) of the buffers; false for an empty or
+// malformed series, or one reaching past `limit` elements (limit < 0: none),
+// which is then reported in *status (if given) and left untouched.
+__device__ __forceinline__ bool series_of(const int64_t* offsets, int32_t N, int q, int64_t limit, int* status,
+                                          int64_t& a, int64_t& n)
 {
-    __shared__ FF red[kNormThreads / 32];
-    const int q = blockIdx.x;
-    int64_t a, n;
     if (offsets) {
         a = offsets[q];
         n = offsets[q + 1] - a;
-        if (a < 0 || n <= 0) return;  // empty (or malformed) series: nothing to write
+        if (a < 0 || n <= 0) return false;
     } else {
         a = static_cast<int64_t>(q) * N;
         n = N;
     }
+    if (limit >= 0 && a + n > limit) {
+        if (status && threadIdx.x == 0) atomicOr(status, sdtw::kStatusBadLength);
+        return false;
+    }
+    return true;
+}
+
+// one CTA per series: long series, and ragged batches (lengths on the device)
+__global__ void __launch_bounds__(kNormThreads)
+znorm_kernel(const float* in, float* out, const int64_t* offsets, int32_t N, int64_t limit, int* status)
+{
+    __shared__ FF red[kNormThreads / 32];
+    int64_t a, n;
+    if (!series_of(offsets, N, blockIdx.x, limit, status, a, n)) return;
     znorm_series(in + a, out + a, n, threadIdx.x, kNormThreads, [&](FF v) { return block_sum(v, red); });
+}
+
+// The derivative of Eq. 2 applied to a gradient: for z = (x - mean) * inv
+// (inv = 1/S, or 1 for a series with S == 0),
+//   dcost/dx_k = inv * (g_k - mean(g) - z_k * mean(g z))
+// with g = dcost/dz, rewritten in place.  z and inv are recomputed from x with
+// the normaliser's own arithmetic; the two sums are compensated.  One CTA per
+// series.
+__global__ void __launch_bounds__(kNormThreads)
+znorm_vjp_kernel(const float* x, float* g, const int64_t* offsets, int32_t N, int64_t limit)
+{
+    __shared__ FF red[kNormThreads / 32];
+    int64_t a, n;
+    if (!series_of(offsets, N, blockIdx.x, limit, nullptr, a, n)) return;
+    const float* xs = x + a;
+    float* gs = g + a;
+    const int idx = threadIdx.x;
+    const float x0 = xs[0];
+    const float nf = static_cast<float>(n);
+    KSum s1;
+    for (int64_t i = idx; i < n; i += kNormThreads) s1.add(xs[i] - x0);
+    const FF mean = ff_add(FF{x0, 0.f}, ff_div(block_sum(s1.value(), red), nf));
+    KSum s2;
+    for (int64_t i = idx; i < n; i += kNormThreads) {
+        const float c = (xs[i] - mean.hi) - mean.lo;
+        s2.add(c * c);
+    }
+    const float inv = inv_spread(block_sum(s2.value(), red), nf);
+    KSum sg, sgz;
+    for (int64_t i = idx; i < n; i += kNormThreads) {
+        const float z = ((xs[i] - mean.hi) - mean.lo) * inv;
+        sg.add(gs[i]);
+        sgz.add(gs[i] * z);
+    }
+    const FF tg = block_sum(sg.value(), red);
+    const FF tgz = block_sum(sgz.value(), red);
+    const float mg = ff_div(tg, nf).hi, mgz = ff_div(tgz, nf).hi;
+    for (int64_t i = idx; i < n; i += kNormThreads) {
+        const float z = ((xs[i] - mean.hi) - mean.lo) * inv;
+        gs[i] = inv * (gs[i] - mg - z * mgz);
+    }
 }
 
 // The same with 16-byte loads and stores: series of a multiple of 4 samples
@@ -245,16 +299,15 @@ znorm_warp_kernel(const float* in, float* out, int32_t B, int32_t N, bool vec4)
 
 }  // namespace
 
-extern "C" sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N,
-                                       void* stream)
+namespace sdtw {
+
+cudaError_t launch_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N, int64_t limit,
+                              int* status, cudaStream_t st)
 {
-    if (B < 0 || (!offsets && N < 1)) return SDTW_E_INVALID;
-    if (B == 0) return SDTW_OK;
-    if (!in || !out) return SDTW_E_INVALID;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B <= 0) return cudaSuccess;
     // uniform series up to kWarpMaxN samples: a warp each; otherwise (long
     // series, or ragged batches whose lengths live on the device) a CTA each
-    if (!offsets && N <= kWarpMaxN) {
+    if (!offsets && N <= kWarpMaxN && (limit < 0 || static_cast<int64_t>(B) * N <= limit)) {
         const int per = kNormThreads / 32;
         const bool vec4 = N % 4 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
                           reinterpret_cast<uintptr_t>(out) % 16 == 0;
@@ -263,7 +316,29 @@ extern "C" sdtw_status sdtw_znormalize(const float* in, float* out, const int64_
         else
             znorm_warp_kernel<<<(B + per - 1) / per, kNormThreads, 0, st>>>(in, out, B, N, vec4);
     } else {
-        znorm_kernel<<<B, kNormThreads, 0, st>>>(in, out, offsets, N);
+        znorm_kernel<<<B, kNormThreads, 0, st>>>(in, out, offsets, N, limit, status);
     }
-    return cudaGetLastError() == cudaSuccess ? SDTW_OK : SDTW_E_CUDA;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_znorm_vjp(const float* x, float* g, const int64_t* offsets, int32_t B, int32_t N, int64_t limit,
+                             cudaStream_t st)
+{
+    if (B <= 0) return cudaSuccess;
+    znorm_vjp_kernel<<<B, kNormThreads, 0, st>>>(x, g, offsets, N, limit);
+    return cudaGetLastError();
+}
+
+}  // namespace sdtw
+
+extern "C" sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N,
+                                       void* stream)
+{
+    if (B < 0 || (!offsets && N < 1)) return SDTW_E_INVALID;
+    if (B == 0) return SDTW_OK;
+    if (!in || !out) return SDTW_E_INVALID;
+    return sdtw::launch_znormalize(in, out, offsets, B, N, -1, nullptr, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? SDTW_OK
+               : SDTW_E_CUDA;
 }

@@ -33,7 +33,8 @@ class SdtwContext:
     def __init__(self, dtype: str = "f32", device: int | None = None, max_ref_len: int = 100_000,
                  max_batch: int = 512, max_query_len: int = 2000, max_total_query_len: int | None = None,
                  grad: bool = False, keep_checkpoints: bool = False, seg_width: int = 0,
-                 warps_per_query: int = 0, ckpt_stride: int = 0, mem_cap_bytes: int = 0, tile_rows: int = 0):
+                 warps_per_query: int = 0, ckpt_stride: int = 0, mem_cap_bytes: int = 0, tile_rows: int = 0,
+                 znorm_queries: bool = False):
         lib_dtype = {"f32": capi.SDTW_F32, "i8": capi.SDTW_I8}[dtype]
         cfg = capi.sdtw_config_init()
         cfg.dtype = lib_dtype
@@ -48,7 +49,8 @@ class SdtwContext:
         cfg.mem_cap_bytes = int(mem_cap_bytes)
         cfg.tile_rows = int(tile_rows)
         cfg.flags = (capi.SDTW_FLAG_GRAD if grad or keep_checkpoints else 0) | \
-            (capi.SDTW_FLAG_KEEP_CHECKPOINTS if keep_checkpoints else 0)
+            (capi.SDTW_FLAG_KEEP_CHECKPOINTS if keep_checkpoints else 0) | \
+            (capi.SDTW_FLAG_ZNORM_QUERIES if znorm_queries else 0)
         st, h = capi.sdtw_create(cfg)
         capi.check(st, "sdtw_create")
         self.handle = h

@@ -91,6 +91,10 @@ def test_argument_checks_before_device_work(lib):
     cfg = capi.sdtw_config_init()
     cfg.seg_width = 5
     assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_INVALID
+    cfg = capi.sdtw_config_init()
+    cfg.dtype = capi.SDTW_I8
+    cfg.flags = capi.SDTW_FLAG_ZNORM_QUERIES
+    assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_INVALID       # query normalisation is FP32 only
     assert capi.sdtw_forward(None, 1, 10, 1, None, 1, 5, 1, 1, None) == capi.SDTW_E_INVALID
     assert capi.sdtw_backward(None, 1, 10, 1, None, 1, 5, 1, 1, 1, 1, None, None) == capi.SDTW_E_INVALID
     assert capi.sdtw_last_device_status(None, None) == capi.SDTW_E_INVALID

@@ -373,3 +373,79 @@ def test_znorm_batch_layouts(oracle_mod):
     offs = np.array([0, 3, 3, 17, 30])
     r = oracle_mod.znormalize_batch(v, offsets=offs)
     assert np.array_equal(r[3:17], oracle_mod.znormalize(v[3:17])) and np.array_equal(r[17:], oracle_mod.znormalize(v[17:]))
+
+
+# ------------------------------------------- derivative of the normalisation --
+
+def _central(f, x, k, h):
+    xp, xm = x.copy(), x.copy()
+    xp[k] += h
+    xm[k] -= h
+    return (f(xp) - f(xm)) / (2.0 * h)
+
+
+def test_znorm_vjp_matches_central_differences_of_a_smooth_loss(oracle_mod):
+    """d/dx of L(znorm(x)) for a smooth L (a weighted sum plus half the
+    squares, so dL/dz = w + z), against FP64 central differences."""
+    rng = np.random.default_rng(21)
+    for n in (2, 5, 37, 400):
+        x = rng.standard_normal(n) * 3.0 + 7.0
+        w = rng.standard_normal(n)
+        loss = lambda v: float(np.dot(w, oracle_mod.znormalize(v)) + 0.5 * np.sum(oracle_mod.znormalize(v) ** 2))  # noqa: E731
+        gx = oracle_mod.znormalize_vjp(x, w + oracle_mod.znormalize(x))
+        for k in range(min(n, 12)):
+            fd = _central(loss, x, k, 1e-5)
+            assert abs(fd - gx[k]) <= 1e-6 * max(1.0, np.abs(gx).max()), (n, k, fd, gx[k])
+
+
+def test_znorm_vjp_invariants(oracle_mod):
+    """Eq. 2 is invariant to a shift and a positive scale of x, so its
+    derivative is orthogonal to the all-ones vector and to x itself; a
+    gradient along z or along ones has no effect (z is normalised)."""
+    rng = np.random.default_rng(22)
+    x = rng.standard_normal(50) * 2.0 - 1.0
+    g = rng.standard_normal(50)
+    gx = oracle_mod.znormalize_vjp(x, g)
+    assert abs(gx.sum()) <= 1e-12 * np.abs(gx).max() * 50
+    assert abs(np.dot(gx, x)) <= 1e-11 * np.abs(gx).max() * np.abs(x).sum()
+    z = oracle_mod.znormalize(x)
+    assert np.abs(oracle_mod.znormalize_vjp(x, z)).max() <= 1e-12
+    assert np.abs(oracle_mod.znormalize_vjp(x, np.ones(50))).max() <= 1e-12
+    # zero spread: only centred, so the derivative removes the mean
+    c = np.full(8, 3.5)
+    assert np.allclose(oracle_mod.znormalize_vjp(c, np.arange(8.0)), np.arange(8.0) - 3.5, atol=1e-15)
+
+
+def test_cost_of_normalised_query_gradient_matches_central_differences(oracle_mod):
+    """The path gradient with respect to z = znorm(x), carried to x by the
+    normalisation's derivative, against central differences of
+    cost(ref, znorm(x)) where the path is stable."""
+    w = inputs.grad_subset()
+    y = w.ref.astype(np.float64)
+    h = 1e-6
+    checked = 0
+    for q in range(3):
+        x = w.query(q).astype(np.float64) * 1.7 + 0.3   # raw, not normalised
+        z = oracle_mod.znormalize(x)
+        c, e = oracle_mod.forward(z, y)
+        cells, _ = oracle_mod.walkback(z, y, e)
+        gz, _ = oracle_mod.path_gradient(z, y, cells, g=1.0)
+        gx = oracle_mod.znormalize_vjp(x, gz)
+
+        def cost_on_path(v):
+            zz = oracle_mod.znormalize(v)
+            cc, ee = oracle_mod.forward(zz, y)
+            cp, _ = oracle_mod.walkback(zz, y, ee)
+            return cc if cp.shape == cells.shape and np.array_equal(cp, cells) else None
+
+        for k in range(0, len(x), 4):
+            xp, xm = x.copy(), x.copy()
+            xp[k] += h
+            xm[k] -= h
+            fp, fm = cost_on_path(xp), cost_on_path(xm)
+            if fp is None or fm is None:
+                continue
+            fd = (fp - fm) / (2.0 * h)
+            assert abs(fd - gx[k]) <= 1e-5 * max(1.0, np.abs(gx).max()), (q, k, fd, gx[k])
+            checked += 1
+    assert checked >= 24
