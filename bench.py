@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -79,7 +80,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary): SDTW_CLOCKS_DIR, else the temp directory
+        self.path = os.path.join(os.environ.get("SDTW_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"sdtw_clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
