@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     const float* frq = a.fr + static_cast<int64_t>(ql) * a.fr_slot;
     const float* ckq = a.colck + static_cast<int64_t>(ql) * a.ck_slot;
 
-    // walk state, identical in every lane: current cell (wi, wj), the
-    // gradient of row wi and of column wj accumulated so far
+    // walk state: the current cell (wi, wj), identical in every lane, and the
+    // gradients of its row (each lane's share) and column accumulated so far
     int wi = n - 1, wj = static_cast<int>(e64);
     float axl = 0.f, ay = 0.f;  // this lane's share of row wi's gradient; column wj's so far
     bool done = false, first = true;
@@ -286,10 +286,9 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         // may reach past row hi-1: those rows take a left input of +inf (or
         // the left lane's equally invalid rows) and a sample of 0, and are
         // never read -- the walk reads rows up to wi, and a strip's right
-        // neighbour ends its band no lower.
-        // the walk moves up and left from (wi, wj): strips right of wj's strip dj
-        // are not needed, so the schedule ends when strip dj's last lane has
-        // computed row wi
+        // neighbour ends its band no lower.  The walk moves up and left from
+        // (wi, wj), so the strips right of wj's strip dj are not needed either:
+        // the schedule ends when strip dj's last lane has computed row wi.
         const int steps = (wi - rtop) / RS + 4 * dj + 4;
         const int hi = min(re, wi + 1);  // this lane's rows end here
         float last[RS];                  // right-hand cells of the lane's previous rows
