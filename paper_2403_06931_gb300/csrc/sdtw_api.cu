@@ -698,6 +698,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
     if (B == 0) return SDTW_E_INVALID;
+    if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool ragged = offsets != nullptr;
     // every timed run reads the queries the fill would read
