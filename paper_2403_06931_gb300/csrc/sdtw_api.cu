@@ -1,6 +1,7 @@
 // C ABI of the sDTW library (include/sdtw.h): contexts, argument checks,
 // device workspace, launch plans and the autotuner, host-buffer entry points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -356,6 +357,18 @@ bool keep_fits(const sdtw_ctx* c, int32_t B, int32_t N, int64_t M, const FwdPlan
 
 }  // namespace
 
+// A profiler range (NVTX) over one call of the library, so that a timeline
+// tool attributes the call's launches; without a tool attached it costs a
+// test of a null function pointer.
+namespace {
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
+}  // namespace
+
 extern "C" {
 
 int32_t sdtw_abi_version(void) { return SDTW_ABI_VERSION; }
@@ -388,6 +401,7 @@ sdtw_status sdtw_config_init(sdtw_config* cfg)
 
 sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
 {
+    CallRange range("sdtw_create");
     if (!out || !cfg) return SDTW_E_INVALID;
     *out = nullptr;
     if (cfg->dtype != SDTW_F32 && cfg->dtype != SDTW_I8) return SDTW_E_INVALID;
@@ -447,6 +461,7 @@ sdtw_status sdtw_destroy(sdtw_ctx* ctx)
 sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
                          int32_t B, int32_t N, void* cost, int64_t* end, void* stream)
 {
+    CallRange range("sdtw_forward");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
@@ -566,6 +581,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
                           int32_t B, int32_t N, const int64_t* end, const float* grad_cost, float* grad_queries,
                           float* grad_ref, int32_t* path, void* stream)
 {
+    CallRange range("sdtw_backward");
     if (!ctx) return SDTW_E_INVALID;
     if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
     if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
@@ -585,6 +601,7 @@ sdtw_status sdtw_backward(sdtw_ctx* ctx, const float* ref, int64_t M, const floa
 sdtw_status sdtw_path(sdtw_ctx* ctx, const float* ref, int64_t M, const float* queries, const int64_t* offsets,
                       int32_t B, int32_t N, const int64_t* end, int32_t* path, void* stream)
 {
+    CallRange range("sdtw_path");
     if (!ctx) return SDTW_E_INVALID;
     if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
     if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
@@ -599,6 +616,7 @@ sdtw_status sdtw_path(sdtw_ctx* ctx, const float* ref, int64_t M, const float* q
 sdtw_status sdtw_forward_host(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
                               int32_t B, int32_t N, void* cost, int64_t* end, void* stream)
 {
+    CallRange range("sdtw_forward_host");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
     if (B == 0) return SDTW_OK;
@@ -636,6 +654,7 @@ sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t 
                                        float* cost, int64_t* end, float* grad_queries, float* grad_ref,
                                        int32_t* path, void* stream)
 {
+    CallRange range("sdtw_forward_backward_host");
     if (!ctx) return SDTW_E_INVALID;
     if (ctx->cfg.dtype != SDTW_F32) return SDTW_E_UNSUPPORTED;
     if (!(ctx->cfg.flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
@@ -695,6 +714,7 @@ sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t 
 sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries, const int64_t* offsets,
                           int32_t B, int32_t N, void* cost, int64_t* end, void* stream, sdtw_plan* plan)
 {
+    CallRange range("sdtw_autotune");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
     if (B == 0) return SDTW_E_INVALID;

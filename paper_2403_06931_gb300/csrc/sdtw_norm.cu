@@ -22,6 +22,7 @@
 // passes; longer ones are read three times (the second and third reads hit
 // L2 for query-sized series).  HBM sees one read and one write per sample.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
@@ -329,16 +330,21 @@ cudaError_t launch_znorm_vjp(const float* x, float* g, const int64_t* offsets, i
     return cudaGetLastError();
 }
 
+sdtw_status znormalize_call(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N, cudaStream_t st)
+{
+    if (B < 0 || (!offsets && N < 1)) return SDTW_E_INVALID;
+    if (B == 0) return SDTW_OK;
+    if (!in || !out) return SDTW_E_INVALID;
+    return launch_znormalize(in, out, offsets, B, N, -1, nullptr, st) == cudaSuccess ? SDTW_OK : SDTW_E_CUDA;
+}
+
 }  // namespace sdtw
 
 extern "C" sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N,
                                        void* stream)
 {
-    if (B < 0 || (!offsets && N < 1)) return SDTW_E_INVALID;
-    if (B == 0) return SDTW_OK;
-    if (!in || !out) return SDTW_E_INVALID;
-    return sdtw::launch_znormalize(in, out, offsets, B, N, -1, nullptr, static_cast<cudaStream_t>(stream)) ==
-                   cudaSuccess
-               ? SDTW_OK
-               : SDTW_E_CUDA;
+    nvtxRangePushA("sdtw_znormalize");
+    const sdtw_status st = sdtw::znormalize_call(in, out, offsets, B, N, static_cast<cudaStream_t>(stream));
+    nvtxRangePop();
+    return st;
 }
