@@ -182,7 +182,9 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
  *   ref, queries, offsets, B, N, M: as in sdtw_forward (float).
  *   end         device int64 [B]: the end columns sdtw_forward returned.
  *   grad_cost   device float [B]: upstream gradient of each cost.
- *   grad_queries device float, same layout as queries: overwritten.
+ *   grad_queries device float, same layout as queries: overwritten (with
+ *               SDTW_FLAG_ZNORM_QUERIES: the gradient with respect to the raw
+ *               queries passed in, through their normalisation).
  *   grad_ref    device float [M]: overwritten with the sum over queries
  *               (summed in query order: deterministic).
  *   path        device int32, NULL or 2 per query sample: for row i of query q
