@@ -31,8 +31,11 @@
 //
 // The bottom-row minimum (Section 5.2 aggregates it while the last row is
 // produced) is kept per thread as a running (value, column) pair updated with
-// a strict '<' in increasing column order, then reduced over the CTA
-// lexicographically, so the smallest end column wins exact ties.
+// a strict '<' in increasing column order -- from the strip's latest row after
+// the tile when the query's last row ends a tile, else inside the tile that
+// holds it, on the steps where some lane of the warp holds that tile -- then
+// reduced over the CTA lexicographically, so the smallest end column wins
+// exact ties.
 //
 // FP32 accuracy.  D grows along the query (to ~10^3 for N = 2,000), so one
 // rounding of an FP32 cell costs ~10^-4 absolute, and the minimum over near-tied
