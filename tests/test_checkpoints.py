@@ -476,6 +476,8 @@ def kernel_backward(fw, pl, end, RS=None):
                 st["last"] = ls[:]
                 st["dg"] = lefts[RS - 1]
                 for h in range(RS):
+                    # the kernel's shared choice buffer holds RT*kChunk + 7*RT + 32*RS rows
+                    assert 0 <= RS * sg + h < RT * KC + 7 * RT + 32 * RS, (sg, h)
                     dirs[(RS * sg + h, lane)] = codes[h]
         if first:
             lj, kj = (wj - c0) // WB, (wj - c0) % WB
@@ -483,6 +485,8 @@ def kernel_backward(fw, pl, end, RS=None):
             first = False
         # the walk, 32 cells of a row at a time
         while True:
+            # the kernel's per-row gradient shares: RT*kChunk + 7*RT rows from rtop
+            assert 0 <= wi - rtop < RT * KC + 7 * RT, (wi, rtop)
             if wi == 0:
                 cells.append((0, wj))
                 done = True
