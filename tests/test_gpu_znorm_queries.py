@@ -132,3 +132,47 @@ def test_ragged_query_past_the_copy_is_flagged(gpu):
     c = cost.cpu().numpy()
     assert c[-1] == -7.0 and end.cpu().numpy()[-1] == -9   # the last query was skipped
     ctx.close()
+
+
+def _ckpt_floats_per_query(M, N, W, P, RT):
+    """Backward workspace per query (floats) of a checkpointing plan, as the
+    library documents it: the wavefront slot, the boundary columns, a gradient
+    row and 7 scalars."""
+    S, lag_last = 32 * P * W, (P - 1) * 64 + 31
+    nsw, nt = -(-M // S), -(-N // RT)
+    total = (nsw - 1) * max(nt, lag_last + 32) + nt + lag_last
+    fr = -(-total // 32) * 32 * P * (W + (4 if RT == 2 else 8))
+    ck = (-(-M // (8 * W)) - 1) * (-(-N // 4) * 4)
+    return fr + ck + M + 7
+
+
+def test_chunked_backward_with_normalised_queries(gpu):
+    """Kept checkpoints, a backward that re-runs the forward, and a memory cap
+    that holds the checkpoints of 4 of the 9 queries (chunks of 4, 4 and 1,
+    each re-running its forward on the normalised copy) agree bit for bit."""
+    w = inputs.tiny(B=9, N=200, M=4000, seed=306)
+    raw, _ = _raw(w, 6)
+    st = dict(seg_width=16, tile_rows=4, warps_per_query=2)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qr = torch.from_numpy(raw).to(gpu)
+    g = torch.from_numpy(np.linspace(-1.5, 2.0, w.B).astype(np.float32)).to(gpu)
+
+    def run(keep, cap=0):
+        ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True, keep_checkpoints=keep,
+                          znorm_queries=True, mem_cap_bytes=cap, **st)
+        cost, end = ctx.forward(ref, qr)
+        gq, gr, path = ctx.backward(ref, qr, end, g, want_path=True)
+        assert ctx.device_status() == capi.SDTW_OK
+        ctx.close()
+        return [t.cpu().numpy() for t in (cost, end, gq, gr, path)]
+
+    a = run(True)
+    b = run(False)
+    # status, work counter and order (8 + 4 B bytes), the normalised copy (4 B N),
+    # per-query cost and end scratch (12 B), then the arena
+    fixed = 8 + 4 * w.B + 4 * w.B * w.N + 12 * w.B
+    per_q = _ckpt_floats_per_query(w.M, w.N, 16, 2, 4)
+    c = run(False, fixed + 4 * (4 * per_q + 32) + 8)
+    for u, v in ((a, b), (a, c)):
+        for k in range(5):
+            assert np.array_equal(u[k], v[k])
