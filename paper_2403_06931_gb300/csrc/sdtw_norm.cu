@@ -21,6 +21,10 @@
 // Series of up to 2,048 samples stay in the warp's registers between the
 // passes; longer ones are read three times (the second and third reads hit
 // L2 for query-sized series).  HBM sees one read and one write per sample.
+//
+// For queries the library normalises itself, the derivative of Eq. 2
+// (znorm_vjp_kernel) carries a gradient with respect to the normalised series
+// back to the raw one.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
