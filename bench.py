@@ -485,9 +485,15 @@ def cpu_baseline(args, w=None):
     oracle_step(w, idx, threads)
     dt = time.perf_counter() - t0
     cells = k * w.N * w.M
+    # one core: the forward and walk-back of one query on a single thread
+    t1 = time.perf_counter()
+    oracle_step(w, [k % w.B], 1)
+    dt1 = time.perf_counter() - t1
     return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": threads, "kind": "oracle",
             "sample": f"{k} of {w.B} queries ({w.N} x {w.M}): FP64 forward on {threads} threads, then walk-back "
-                      f"+ path gradient on {walkback_threads(w, threads)} threads, {dt:.1f} s"}
+                      f"+ path gradient on {walkback_threads(w, threads)} threads, {dt:.1f} s",
+            "one_core": {"value": round(w.N * w.M / dt1 / 1e9, 4), "unit": "GCUPS",
+                         "sample": f"1 query, forward + walk-back + path gradient on 1 thread, {dt1:.1f} s"}}
 
 
 def run_reference(args):
