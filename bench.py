@@ -303,7 +303,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"sdtw_fp32_{B}x{N}_vs_{M}: forward (cost, end, checkpoints) + backward "
                                "(walk-back gradients)", "B": B, "N": N, "M": M, "cells_per_step": cells,
-                   "plan": tuned, "l2": "flushed (512 MiB write) before every timed step",
+                   "seed": inputs.SEED_BASE + 2 + rank, "plan": tuned,
+                   "l2": "flushed (512 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}, no collective on the data path"},
         "fwd_gcups": round(cells / (fwd_avg * 1e-3) / 1e9, 2),
         "bwd_gcups": round(cells / (sum(bwd_ms) / len(bwd_ms) * 1e-3) / 1e9, 2),
@@ -316,6 +317,7 @@ def run_ours(args, rank, world, local_rank):
                 "api": "sdtw_forward_backward_host (pinned host buffers)"},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
+        "device": {"name": torch.cuda.get_device_name(dev), "sms": sms},
         "forms": forms,
     }
     if not args.no_cpu_baseline and world == 1:   # the host baseline belongs to the 1-GPU line
