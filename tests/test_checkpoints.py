@@ -543,3 +543,18 @@ def test_kernel_band_schedule_and_walk(P, W, RT, n, M, two_rows):
     full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
     assert cells == full
     assert bands > 1
+
+
+def test_kernel_schedule_random_shapes():
+    """Seeded random plans, shapes and step heights for the backward's lane
+    schedule: the banded walk equals the walk over the whole FP32 matrix and
+    the end cell is recomputed bit for bit."""
+    rng = np.random.default_rng(4242)
+    for _ in range(20):
+        P, W, RT = int(rng.choice([1, 2])), int(rng.choice([4, 8])), int(rng.choice([2, 4]))
+        RS = int(rng.choice([1, 2, RT]))
+        n, M = int(rng.integers(1, 240)), int(rng.integers(2, 1300))
+        pl, fw = _setup(P, W, RT, n, M, seed=int(rng.integers(0, 10**6)))
+        cells, v_end, _ = kernel_backward(fw, pl, fw["end"], RS=RS)
+        assert v_end == fw["cost"], (P, W, RT, RS, n, M)
+        assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"]), (P, W, RT, RS, n, M)

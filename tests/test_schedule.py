@@ -247,3 +247,19 @@ def test_schedule_checkpoints(oracle_mod, RT, R, N):
             # D(i, col): last row of the query prefix x[:i+1] at column col
             _, _, row = oracle_mod.forward(x[:i + 1], y[:col + 1], last_row=True)
             assert ck[(b, i)] == row[col]
+
+
+def test_schedule_random_shapes(oracle_mod):
+    """Seeded random plans and shapes (lengths not multiples of the tile, the
+    strip or the sweep; queries shorter than a warp; references shorter than a
+    strip): every shared-memory access checked, the last row equal to the
+    oracle's, the end column its first minimum."""
+    rng = np.random.default_rng(2024)
+    for _ in range(20):
+        P, W, RT = int(rng.choice([1, 2, 3])), int(rng.choice([2, 4, 8])), int(rng.choice([2, 4]))
+        n, M = int(rng.integers(1, 300)), int(rng.integers(1, 2000))
+        x, y = rng.standard_normal(n), rng.standard_normal(M)
+        last_row, _, _ = simulate_forward(x, y, P, W, RT=RT)
+        c, e, row = oracle_mod.forward(x, y, last_row=True)
+        assert np.array_equal(last_row, row), (P, W, RT, n, M)
+        assert np.min(last_row) == c and int(np.argmin(last_row)) == e
