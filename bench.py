@@ -274,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
 
     forms = {}
     if rank == 0 and not args.no_forms:
-        forms = run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev)
+        forms["autograd"] = run_autograd_form(args, ctx, ref, qs, B, N, M, flush, stream)
+        forms.update(run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev))
 
     ctx.close()
     if rank != 0:
@@ -323,6 +324,43 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline and world == 1:   # the host baseline belongs to the 1-GPU line
         out["cpu_baseline"] = cpu_baseline(args, w)
     return out
+
+
+def run_autograd_form(args, ctx, ref, qs, B, N, M, flush, stream):
+    """The differentiable step as a PyTorch user runs it: sdtw_cost (the
+    torch.autograd.Function over sdtw_forward) and .backward() (sdtw_backward,
+    then the device-status check, which synchronises the stream), on the
+    headline's context and batch, L2 flushed before each step."""
+    import torch
+
+    from paper_2403_06931_gb300.sdtw import sdtw_cost
+
+    r = ref.detach().clone().requires_grad_(True)
+    x = qs.detach().clone().requires_grad_(True)
+    gc = torch.ones(B, device=ref.device)
+
+    def step():
+        r.grad = None
+        x.grad = None
+        c, _ = sdtw_cost(r, x, ctx)
+        c.backward(gc)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = sum(ts) / len(ts)
+    return {"gcups": round(B * N * M / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3),
+            "api": "sdtw_cost(ref, queries, ctx) then cost.backward(): forward with checkpoints, backward, "
+                   "device-status check"}
 
 
 def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
@@ -413,16 +451,23 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
         rplan = rctx.plan(wr.B, Nr, wr.M, ragged=True) if args.no_autotune else rctx.autotune(rr, qr, offsets=orr, N=Nr)
         rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
         torch.cuda.synchronize()
+        eager_c, eager_e = cr.clone(), er.clone()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
+        # the replayed graph must reproduce the eager call bit for bit before it is timed
+        cr.fill_(float("nan"))
+        er.fill_(-7)
         g.replay()
         torch.cuda.synchronize()
+        if not (torch.equal(cr, eager_c) and torch.equal(er, eager_e)):
+            raise RuntimeError("ragged forward replayed from a CUDA graph differs from the eager call")
         ms = timed(g.replay, 3)
         assert rctx.device_status() == capi.SDTW_OK
         forms["ragged_persistent_graph"] = {
             "workload": wr.name, "cells": wr.cells, "gcups": round(wr.cells / (ms * 1e-3) / 1e9, 2),
-            "ms": round(ms, 3), "plan": rplan, "launch": "one persistent kernel, replayed from a CUDA graph"}
+            "ms": round(ms, 3), "plan": rplan, "launch": "one persistent kernel, replayed from a CUDA graph",
+            "replay_equals_eager": True}
         rctx.close()
     return forms
 
@@ -467,6 +512,26 @@ def oracle_step(w, idx, threads):
         list(ex.map(back, range(len(idx))))
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def host_threads():
     return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
 
@@ -492,6 +557,7 @@ def cpu_baseline(args, w=None):
     oracle_step(w, [k % w.B], 1)
     dt1 = time.perf_counter() - t1
     return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{k} of {w.B} queries ({w.N} x {w.M}): FP64 forward on {threads} threads, then walk-back "
                       f"+ path gradient on {walkback_threads(w, threads)} threads, {dt:.1f} s",
             "one_core": {"value": round(w.N * w.M / dt1 / 1e9, 4), "unit": "GCUPS",
@@ -521,7 +587,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"sdtw_fp32_{w.B}x{w.N}_vs_{w.M}: oracle forward + walk-back gradient, "
                                    f"{k}-query sample per step", "B": w.B, "N": w.N, "M": w.M},
-            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": threads, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"{k} of {w.B} queries per step, warm-up on 1 query"},
             "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

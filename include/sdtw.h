@@ -29,8 +29,9 @@
  *     returned after a failed launch.  No C++ exception crosses this ABI.
  *   - Errors found on the device (a query longer than N in a ragged batch, an
  *     end index out of range) are recorded in the context's device status word
- *     and reported by sdtw_last_device_status; the affected query's outputs are
- *     left unwritten.
+ *     and reported by sdtw_last_device_status.  A forward writes the empty
+ *     query's outputs for such a query (cost = +inf, or INT32_MAX in SDTW_I8;
+ *     end = -1); a backward leaves that query's gradient entries unwritten.
  *   - A context is not thread-safe: use one context per host thread / stream.
  *   - Inputs must be finite.  Inputs are used as given; z-normalisation (the
  *     paper's Eq. 2) is the caller's step (sdtw_znormalize), or the
@@ -55,16 +56,21 @@ typedef enum sdtw_status {
     SDTW_E_INVALID = 1,     /* bad argument (null pointer, N<1, M<1, B<0, dtype mismatch, size over a configured maximum) */
     SDTW_E_NOMEM = 2,       /* device or host workspace could not be allocated, or would exceed mem_cap_bytes */
     SDTW_E_CUDA = 3,        /* a CUDA runtime call failed; the CUDA error text is kept in the context */
-    SDTW_E_TIMEOUT = 4,     /* a bounded device-side wait ran out (reported by sdtw_last_device_status) */
+    SDTW_E_TIMEOUT = 4,     /* reserved for a bounded device-side wait that ran out; no kernel of this build waits */
     SDTW_E_UNSUPPORTED = 5  /* a valid request this build does not implement (e.g. backward in int8 mode) */
 } sdtw_status;
 
 typedef enum sdtw_dtype {
     SDTW_F32 = 0, /* float inputs, float costs, FP32 arithmetic (fused multiply-add) */
-    SDTW_I8 = 1   /* int8 inputs, int32 costs, exact integer arithmetic */
+    SDTW_I8 = 1,  /* int8 inputs, int32 costs, exact integer arithmetic */
+    SDTW_U8 = 2,  /* uint8 codebook codes (sdtw_codebook_encode), int32 costs in units of the codebook's
+                     step^2, exact integer arithmetic */
+    SDTW_F16 = 3  /* the paper's precision: IEEE binary16 inputs, every operation of Eq. 1 rounded to binary16
+                     (two queries per thread as __half2), float costs holding the binary16 result; uniform
+                     batches only (no offsets) */
 } sdtw_dtype;
 
-/* sdtw_config.flags */
+/* sdtw_config.flags (SDTW_I8 and SDTW_U8 contexts run the forward only) */
 #define SDTW_FLAG_GRAD 0x1u             /* the context will run sdtw_backward: size checkpoint workspace */
 #define SDTW_FLAG_KEEP_CHECKPOINTS 0x2u /* sdtw_forward also stores the checkpoints sdtw_backward needs */
 #define SDTW_FLAG_NO_AUTOTUNE 0x4u      /* use the built-in default plan instead of timing candidates */
@@ -90,10 +96,11 @@ typedef struct sdtw_config {
     int32_t seg_width;           /* reference columns per thread (the paper's segment width): 8, 16, 20, 24, 28
                                     or 32; 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
-    int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints; 0 = 32 (the only stride this build has) */
+    int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints: 16, 32 or 64; 0 = chosen by
+                                    the library (16, or the autotuner's choice) */
     int32_t reserved0;           /* must be 0 */
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
-    uint64_t spin_limit;         /* iteration bound for device-side waits; 0 = default */
+    uint64_t spin_limit;         /* reserved: no kernel of this build waits on a flag; must be 0 */
     uint32_t flags;              /* SDTW_FLAG_* */
     int32_t tile_rows;           /* query rows a thread advances per step (2 or 4); 0 = chosen by the library */
 } sdtw_config;
@@ -131,7 +138,9 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * *out receives the context, or NULL on error.
  * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
  * SDTW_FLAG_GRAD with SDTW_I8, an unsupported seg_width or tile_rows, a
- * non-zero reserved0), SDTW_E_UNSUPPORTED (a ckpt_stride other than 0 or 32),
+ * non-zero reserved0 or spin_limit, a negative ckpt_stride),
+ * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 16, 32 or 64, or a
+ * max_query_len no forward plan can stage in shared memory),
  * SDTW_E_NOMEM (workspace above mem_cap_bytes, too small for one query's
  * checkpoints, or allocation failure), SDTW_E_CUDA (device unusable). */
 sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg);
@@ -159,7 +168,7 @@ sdtw_status sdtw_destroy(sdtw_ctx* ctx);
  * the whole batch's checkpoints fit the context's workspace (otherwise the
  * backward re-runs the forward in chunks of queries).
  * Errors: SDTW_E_INVALID (null pointers with B > 0, N < 1, M < 1, sizes above
- * the context maxima; SDTW_I8 needs N <= 33,000 so int32 costs cannot
+ * the context maxima; SDTW_I8 and SDTW_U8 need N <= 32,896 so int32 costs cannot
  * overflow), SDTW_E_UNSUPPORTED (N too long for shared memory), SDTW_E_CUDA.
  */
 sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
@@ -173,9 +182,11 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
  * smallest D, exact ties to the first of that list, column 0 upwards, stopping
  * at row 0).  The DP is recomputed band by band from checkpoints of the
  * forward: its wavefront (an anti-diagonal staircase of rows, one per thread)
- * every ckpt_stride steps, and the boundary column of every K-column window
- * (K = 8 * seg_width); each band is recomputed with the forward's own FP32
- * operations, so the values are the forward's bit for bit.  The full matrix is
+ * every ckpt_stride steps (16, 32 or 64), and the boundary column of every
+ * K-column window (K = 8 * seg_width); a band (one window, one stride of
+ * steps) is recomputed with the forward's own FP32 operations, so the values
+ * are the forward's bit for bit.  A shorter stride makes each band change of
+ * the walk cheaper and doubles the checkpoint memory.  The full matrix is
  * never stored.  Under mem_cap_bytes the batch may run in chunks of queries,
  * each re-running its forward with checkpoint stores.
  * Along the path, d cost/d x_i += 2 (x_i - y_j) and d cost/d y_j += -2 (x_i - y_j).
@@ -251,7 +262,9 @@ sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t 
  * the batch's checkpoints, each candidate is timed as a forward with
  * checkpoint stores followed by the backward (with zero upstream gradients
  * into scratch it allocates for the call), so the plan serves the
- * differentiable step.  Runs several forwards on `stream` and synchronises
+ * differentiable step; the checkpoint stride (16, 32 or 64 steps, unless the
+ * config fixes it) is then one more axis, and a stride whose checkpoints do
+ * not fit the workspace under mem_cap_bytes is not a candidate.  Runs several forwards on `stream` and synchronises
  * it.  Arguments as sdtw_forward; cost/end are scratch outputs.  *plan (if not
  * NULL) receives the chosen plan.  Errors: as sdtw_forward, and SDTW_E_NOMEM
  * when the backward's scratch cannot be allocated.
@@ -287,6 +300,32 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
 sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets, int32_t B, int32_t N,
                             void* stream);
 
+/*
+ * Reference codebook (paper Section 8, future work: quantise below fp16 to
+ * uint8 with a codebook built from the reference, dividing the bulk of the
+ * reference's value distribution evenly over the 256 codes and clamping
+ * outliers to the extreme codes).  The bulk is mean +- sigmas * S of the
+ * reference (population spread S); code k covers [lo + k step, lo + (k+1) step)
+ * with step = 2 sigmas S / 256.  A forward on a context of dtype SDTW_U8 over
+ * codes of the reference and of the queries then returns exact int32 costs
+ * sum (code_x - code_y)^2, i.e. the squared-difference cost of the quantised
+ * series in units of step^2; the end column follows the same tie rule.
+ *
+ * sdtw_codebook_fit: from the reference (device float [M], M >= 1) writes the
+ *   codebook to params (device float [4]: lo, 1/step, step, 0) on `stream`.
+ *   Statistics in double on one CTA.  A reference with zero spread gets
+ *   step = 1 and lo = mean - 128.  sigmas > 0 (4 keeps 99.99% of a Gaussian).
+ *   Errors: SDTW_E_INVALID (null pointers, M < 1, sigmas not positive and
+ *   finite), SDTW_E_CUDA.
+ * sdtw_codebook_encode: out[i] = clamp(floor((in[i] - lo) * (1/step)), 0, 255),
+ *   the subtraction and the product each rounded to float (device float [n]
+ *   in, device uint8 [n] out, params as written by sdtw_codebook_fit or by the
+ *   caller).  Asynchronous on `stream`; no allocation.  Errors: SDTW_E_INVALID
+ *   (n < 0, null pointers with n > 0), SDTW_E_CUDA.
+ */
+sdtw_status sdtw_codebook_fit(const float* ref, int64_t M, float sigmas, float* params, void* stream);
+sdtw_status sdtw_codebook_encode(const float* in, int64_t n, const float* params, uint8_t* out, void* stream);
+
 /* Largest batch sdtw_forward_noalloc accepts (its fixed device scratch holds
  * the query order for this many queries: 256 KiB per GPU). */
 #define SDTW_NOALLOC_MAX_BATCH 65536
@@ -311,8 +350,9 @@ sdtw_status sdtw_znormalize(const float* in, float* out, const int64_t* offsets,
  * Every call shares the one array: calls that overlap on the GPU (on
  * different streams, or from several host threads) race and must not be
  * issued.  Each call clears the counter and status word itself.  Errors found
- * on the device (a ragged query longer than N) are not reported: that
- * query's outputs are left unwritten.
+ * on the device are not reported (there is no context to read them from): a
+ * ragged query longer than N gets the empty query's outputs (cost = +inf, or
+ * INT32_MAX in SDTW_I8; end = -1).
  * Errors: SDTW_E_INVALID (bad sizes or null pointers as for sdtw_forward,
  * unknown dtype, B > SDTW_NOALLOC_MAX_BATCH), SDTW_E_UNSUPPORTED (N too long
  * for shared memory), SDTW_E_CUDA.

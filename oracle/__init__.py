@@ -60,8 +60,12 @@ def _load():
             lib.sdtw_oracle_walkback_f64.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int64,
                                                      _i, _i, _i, _d]
             lib.sdtw_oracle_znorm_f64.argtypes = [_d, ctypes.c_int64, _d]
+            lib.sdtw_oracle_forward_f16.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, _d, _i, _d]
+            lib.sdtw_oracle_round_f16.argtypes = [_d, ctypes.c_int64, _d]
+            lib.sdtw_oracle_fma_f16.argtypes = [_d, _d, _d, ctypes.c_int64, _d]
             for f in (lib.sdtw_oracle_forward_f64, lib.sdtw_oracle_forward_i64, lib.sdtw_oracle_walkback_f64,
-                      lib.sdtw_oracle_znorm_f64):
+                      lib.sdtw_oracle_znorm_f64, lib.sdtw_oracle_forward_f16, lib.sdtw_oracle_round_f16,
+                      lib.sdtw_oracle_fma_f16):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -100,6 +104,41 @@ def forward(x, y, last_row: bool = False):
                                          _p(row, _d) if last_row else None)
     if rc != 0:
         raise ValueError(f"oracle forward failed (code {rc}) for n={np.size(x)}, m={np.size(y)}")
+    return (c.value, e.value, row) if last_row else (c.value, e.value)
+
+
+def round_f16(values):
+    """Each value rounded to the nearest IEEE binary16 value (ties to even),
+    as float64 (beyond 65504 by half a unit or more: +-inf)."""
+    v = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
+    out = np.empty_like(v)
+    _load().sdtw_oracle_round_f16(_p(v, _d), len(v), _p(out, _d))
+    return out.reshape(np.shape(values))
+
+
+def fma_f16(a, b, c):
+    """fl16(a * b + c) for binary16 values, rounded once, element by element."""
+    a, b, c = (np.ascontiguousarray(np.broadcast_to(t, np.broadcast(a, b, c).shape), dtype=np.float64).reshape(-1)
+               for t in (a, b, c))
+    out = np.empty_like(a)
+    _load().sdtw_oracle_fma_f16(_p(a, _d), _p(b, _d), _p(c, _d), len(a), _p(out, _d))
+    return out
+
+
+def forward_f16(x, y, last_row: bool = False):
+    """sDTW in the paper's binary16 precision (Section 5.2): Eq. 1 with every
+    operation rounded to binary16 (the local cost's subtraction, then one
+    fused multiply-add).  x and y must hold binary16 values (e.g. float16
+    arrays).  Returns (cost, end[, last row]) with the cost as a float."""
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    yv = np.ascontiguousarray(y, dtype=np.float64)
+    c = ctypes.c_double()
+    e = ctypes.c_int64()
+    row = np.empty(len(yv), dtype=np.float64) if last_row else None
+    rc = _load().sdtw_oracle_forward_f16(_p(xv, _d), len(xv), _p(yv, _d), len(yv), ctypes.byref(c), ctypes.byref(e),
+                                         _p(row, _d) if last_row else None)
+    if rc != 0:
+        raise ValueError(f"oracle binary16 forward failed (code {rc}): inputs must be binary16 values")
     return (c.value, e.value, row) if last_row else (c.value, e.value)
 
 
@@ -145,6 +184,32 @@ def znormalize_batch(values, offsets=None, N=None):
     for a, b in bounds:
         out[a:b] = znormalize(v[a:b])
     return out
+
+
+def codebook_fit(ref, sigmas: float = 4.0):
+    """The reference codebook of the paper's Section 8 (future work): the bulk
+    of the reference's value distribution divided evenly into the 256 uint8
+    codes, outliers clamped to the extreme codes.  The bulk is read here as
+    mean +- sigmas * S with the population spread S (FP64, two passes).
+    Returns (lo, step): code k covers [lo + k step, lo + (k + 1) step).  A
+    reference with zero spread gets step 1 and lo = mean - 128."""
+    y = np.asarray(ref, dtype=np.float64)
+    mu = y.sum() / y.shape[0]
+    c = y - mu
+    s = np.sqrt((c * c).sum() / y.shape[0])
+    if not s > 0.0:
+        return mu - 128.0, 1.0
+    return mu - sigmas * s, 2.0 * sigmas * s / 256.0
+
+
+def codebook_encode(values, lo, inv_step):
+    """uint8 codes of values under a codebook: clamp(floor((x - lo) * inv_step),
+    0, 255), the subtraction and the product each rounded to float32 -- the
+    precision in which the library decides a code, so that both sides take
+    every decision alike (lo and inv_step are float32 parameters)."""
+    x = np.asarray(values, dtype=np.float32)
+    t = (x - np.float32(lo)) * np.float32(inv_step)
+    return np.clip(np.floor(t), 0, 255).astype(np.uint8)
 
 
 def default_threads() -> int:

@@ -27,8 +27,10 @@
  *   z-normalisation (Section 5.1, Eq. 2): the standardisation the paper
  *            applies to the reference and every query before the fill.
  *
- * Floating point is double throughout; the integer variant uses int64 and is
- * exact.  Everything is a straightforward row-by-row scalar loop.
+ * Floating point is double throughout, except the binary16 variant (the
+ * paper's own precision, each operation rounded to binary16); the integer
+ * variant uses int64 and is exact.  Everything is a straightforward
+ * row-by-row scalar loop.
  */
 #include <math.h>
 #include <stdint.h>
@@ -143,6 +145,131 @@ int sdtw_oracle_forward_i64(const int64_t* x, int64_t n, const int64_t* y, int64
     *cost = best;
     *end = arg;
     if (last_row) memcpy(last_row, prev, (size_t)m * sizeof(int64_t));
+    free(prev);
+    free(cur);
+    return ORACLE_OK;
+}
+
+/* ----------------------------------------------------------------- f16 -- */
+
+/*
+ * The paper's own precision (Section 5.2 runs its fill in float16, packed as
+ * __half2): Eq. 1 evaluated with every operation rounded to IEEE 754
+ * binary16, round to nearest with ties to even,
+ *     d = fl16(x_i - y_j),   D(i,j) = fl16(d * d + min{ D(i-1,j), D(i,j-1), D(i-1,j-1) }),
+ * the product and the sum rounded once (a fused multiply-add); the minimum is
+ * exact.  Boundaries and the free start and end as in the double version
+ * (row 0: D(0,j) = fl16(d * d + 0)).  Values are carried in doubles, each
+ * one a binary16 value; a sum at or beyond 65520 rounds to +inf.
+ */
+
+/* The binary16 value nearest to v (ties to the even significand).  Normal
+ * binary16 numbers have 11 significant bits, so in [2^(e-1), 2^e) the spacing
+ * is 2^(e-11); below 2^-14 the spacing is that of the subnormals, 2^-24. */
+static double round_f16(double v)
+{
+    if (v == 0.0 || isnan(v) || isinf(v)) return v;
+    const double a = fabs(v);
+    int e;
+    frexp(a, &e);
+    const double ulp = ldexp(1.0, e - 11 < -24 ? -24 : e - 11);
+    const double q = a / ulp;              /* exact: a power-of-two scaling */
+    double r = floor(q);
+    const double f = q - r;                /* exact */
+    if (f > 0.5 || (f == 0.5 && fmod(r, 2.0) != 0.0)) r += 1.0;
+    double res = r * ulp;
+    if (res > 65504.0) res = INFINITY;     /* 65520 and above: beyond the largest finite value */
+    return copysign(res, v);
+}
+
+/* fl16(a * b + c) for binary16 a, b, c, rounded once.  a * b is exact in
+ * double (two 11-bit significands); the sum s = fl64(a * b + c) plus its
+ * exact error t (TwoSum) give the exact value s + t.  Rounding s alone is
+ * right unless s lies exactly halfway between two binary16 values and t != 0,
+ * in which case the exact value lies on t's side of that midpoint. */
+static double fma_f16(double a, double b, double c)
+{
+    const double p = a * b;
+    const double s = p + c;
+    if (isinf(s) || isnan(s)) return s;
+    const double bb = s - p;
+    const double t = (p - (s - bb)) + (c - bb);
+    const double r = round_f16(s);
+    if (t == 0.0 || r == s) return r;
+    /* is s a midpoint?  then the nearer neighbour on t's side wins */
+    const double a_s = fabs(s);
+    int e;
+    frexp(a_s, &e);
+    const double ulp = ldexp(1.0, e - 11 < -24 ? -24 : e - 11);
+    const double q = a_s / ulp;
+    if (q - floor(q) != 0.5) return r;
+    const double lo = copysign(floor(q) * ulp, s), hi = copysign((floor(q) + 1.0) * ulp, s);
+    const double below = s > 0 ? lo : hi, above = s > 0 ? hi : lo;   /* as signed values */
+    const double pick = t > 0 ? above : below;
+    return fabs(pick) > 65504.0 ? copysign(INFINITY, pick) : pick;
+}
+
+/* Test hooks for the two rounding routines (pinned against numpy's float16
+ * conversion and against exact rational arithmetic). */
+int sdtw_oracle_round_f16(const double* in, int64_t n, double* out)
+{
+    if (!in || !out || n < 0) return ORACLE_EINVAL;
+    for (int64_t k = 0; k < n; ++k) out[k] = round_f16(in[k]);
+    return ORACLE_OK;
+}
+
+int sdtw_oracle_fma_f16(const double* a, const double* b, const double* c, int64_t n, double* out)
+{
+    if (!a || !b || !c || !out || n < 0) return ORACLE_EINVAL;
+    for (int64_t k = 0; k < n; ++k) out[k] = fma_f16(a[k], b[k], c[k]);
+    return ORACLE_OK;
+}
+
+/* Eq. 1 in binary16 arithmetic; x and y must hold binary16 values. */
+int sdtw_oracle_forward_f16(const double* x, int64_t n, const double* y, int64_t m,
+                            double* cost, int64_t* end, double* last_row)
+{
+    if (!x || !y || !cost || !end || n < 1 || m < 1) return ORACLE_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(round_f16(x[i]) == x[i]) || isinf(x[i])) return ORACLE_EINVAL;
+    for (int64_t j = 0; j < m; ++j)
+        if (!(round_f16(y[j]) == y[j]) || isinf(y[j])) return ORACLE_EINVAL;
+    double* prev = (double*)malloc((size_t)m * sizeof(double));
+    double* cur = (double*)malloc((size_t)m * sizeof(double));
+    if (!prev || !cur) {
+        free(prev);
+        free(cur);
+        return ORACLE_ENOMEM;
+    }
+    for (int64_t j = 0; j < m; ++j) {
+        const double d = round_f16(x[0] - y[j]);   /* x - y is exact in double */
+        prev[j] = fma_f16(d, d, 0.0);
+    }
+    for (int64_t i = 1; i < n; ++i) {
+        const double d0 = round_f16(x[i] - y[0]);
+        cur[0] = fma_f16(d0, d0, prev[0]);
+        for (int64_t j = 1; j < m; ++j) {
+            double best = prev[j - 1];
+            if (cur[j - 1] < best) best = cur[j - 1];
+            if (prev[j] < best) best = prev[j];
+            const double d = round_f16(x[i] - y[j]);
+            cur[j] = fma_f16(d, d, best);
+        }
+        double* t = prev;
+        prev = cur;
+        cur = t;
+    }
+    double best = prev[0];
+    int64_t arg = 0;
+    for (int64_t j = 1; j < m; ++j) {
+        if (prev[j] < best) {
+            best = prev[j];
+            arg = j;
+        }
+    }
+    *cost = best;
+    *end = arg;
+    if (last_row) memcpy(last_row, prev, (size_t)m * sizeof(double));
     free(prev);
     free(cur);
     return ORACLE_OK;

@@ -25,6 +25,8 @@ SDTW_E_UNSUPPORTED = 5
 # sdtw_dtype
 SDTW_F32 = 0
 SDTW_I8 = 1
+SDTW_U8 = 2
+SDTW_F16 = 3
 
 SDTW_FLAG_GRAD = 0x1
 SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
@@ -94,6 +96,8 @@ SIGNATURES = [
     ("sdtw_get_plan", _ST, [_P, _I32, _I32, _I64, _I32, _I32, ctypes.POINTER(sdtw_plan)]),
     ("sdtw_forward_noalloc", _ST, [ctypes.c_int, _P, _I64, _P, _P, _I32, _I32, _P, _P, _P]),
     ("sdtw_znormalize", _ST, [_P, _P, _P, _I32, _I32, _P]),
+    ("sdtw_codebook_fit", _ST, [_P, _I64, ctypes.c_float, _P, _P]),
+    ("sdtw_codebook_encode", _ST, [_P, _I64, _P, _P, _P]),
     ("sdtw_last_device_status", _ST, [_P, _P]),
     ("sdtw_last_error", ctypes.c_char_p, [_P]),
     ("sdtw_workspace_bytes", ctypes.c_size_t, [_P]),
@@ -208,6 +212,14 @@ SDTW_NOALLOC_MAX_BATCH = 65536
 
 def sdtw_znormalize(inp, out, offsets, B, N, stream) -> int:
     return load().sdtw_znormalize(inp, out, offsets, B, N, stream)
+
+
+def sdtw_codebook_fit(ref, M, sigmas, params, stream) -> int:
+    return load().sdtw_codebook_fit(ref, M, sigmas, params, stream)
+
+
+def sdtw_codebook_encode(inp, n, params, out, stream) -> int:
+    return load().sdtw_codebook_encode(inp, n, params, out, stream)
 
 
 def sdtw_last_device_status(ctx, stream) -> int:

@@ -22,8 +22,14 @@ using sdtw::FwdPlan;
 namespace {
 
 constexpr size_t kDefaultCap = size_t(16) << 30;
-constexpr int kMaxSmem = 227 * 1024;
-constexpr int kI8MaxN = 33000;  // N * 254^2 < 2^31
+constexpr int64_t kMaxSmem = sdtw::kMaxSmemBytes;
+constexpr int kI8MaxN = sdtw::kIntMaxN;
+// steps between the checkpointing forward's wavefront stores when neither the
+// caller nor the autotuner chose: 16-step bands (64 rows with 4-row tiles) make
+// the backward's recompute per band change short
+constexpr int kDefaultStride = 16;
+// the strides the autotuner times for a context that keeps checkpoints
+constexpr int kStrides[] = {16, 32, 64};
 
 struct DevBuf {
     void* p = nullptr;
@@ -57,7 +63,7 @@ struct CkptKey {
     const int64_t* offsets = nullptr;
     int64_t M = 0;
     int32_t B = 0, N = 0;
-    int32_t W = 0, P = 0, RT = 0;
+    int32_t W = 0, P = 0, RT = 0, KS = 0;
     bool valid = false;
 };
 
@@ -88,7 +94,7 @@ struct sdtw_ctx {
     // SDTW_FLAG_ZNORM_QUERIES: the z-normalised queries (max_total_query_len floats)
     float* d_zq = nullptr;
 
-    std::map<TuneKey, std::tuple<int, int, int>> tuned;  // -> (W, P, RT)
+    std::map<TuneKey, std::tuple<int, int, int, int>> tuned;  // -> (W, P, RT, checkpoint stride)
 };
 
 namespace {
@@ -99,7 +105,12 @@ sdtw_status cuda_fail(sdtw_ctx* c, cudaError_t e)
     return SDTW_E_CUDA;
 }
 
-size_t elem_size(sdtw_dtype dt) { return dt == SDTW_I8 ? 1 : 4; }
+size_t elem_size(sdtw_dtype dt) { return dt == SDTW_F32 ? 4 : dt == SDTW_F16 ? 2 : 1; }
+
+bool int_mode(sdtw_dtype dt) { return dt == SDTW_I8 || dt == SDTW_U8; }
+
+// CTAs of a non-persistent launch over nq queries (binary16 runs two queries per CTA)
+int plain_grid(sdtw_dtype dt, int nq) { return dt == SDTW_F16 ? (nq + 1) / 2 : nq; }
 
 sdtw_status dev_alloc(sdtw_ctx* c, void** p, size_t bytes)
 {
@@ -141,17 +152,18 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
 {
     // defaults measured on the paper's batch: 4 rows per thread, four warps
     // per query, and 24 columns per thread for the plain fill, 32 with
-    // checkpoints (forward 16.5-16.7 ms and backward 5.8 ms over its wider
-    // windows: the fastest differentiable step)
+    // checkpoints (the backward's wider windows give fewer band changes)
     FwdPlan p;
     p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : 24);
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
     p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
+    p.KS = c->cfg.ckpt_stride > 0 ? c->cfg.ckpt_stride : kDefaultStride;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
         if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
         if (c->cfg.warps_per_query <= 0) p.P = std::get<1>(it->second);
         if (c->cfg.tile_rows <= 0) p.RT = std::get<2>(it->second);
+        if (c->cfg.ckpt_stride <= 0) p.KS = std::get<3>(it->second);
     }
     // a short reference needs fewer threads per query (unless the caller fixed P)
     if (c->cfg.warps_per_query <= 0)
@@ -160,10 +172,12 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
     p.smem = sdtw::fwd_smem_bytes(c->cfg.dtype, N, p.P, p.W, p.RT);
     p.persistent = ragged;
     if (p.persistent) {
-        int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
+        // 0 CTAs per SM when the query does not fit in shared memory: the call
+        // then fails with SDTW_E_UNSUPPORTED before any launch
+        const int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
         p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
     } else {
-        p.grid = B;
+        p.grid = plain_grid(c->cfg.dtype, B);
     }
     return p;
 }
@@ -176,7 +190,7 @@ sdtw_status check_common(sdtw_ctx* c, const void* ref, int64_t M, const void* qu
     if (M > c->cfg.max_ref_len || N > c->cfg.max_query_len || B > c->cfg.max_batch) return SDTW_E_INVALID;
     if (M > INT_MAX / 2) return SDTW_E_INVALID;
     if (B > 0 && (!ref || !queries || !o1 || !o2)) return SDTW_E_INVALID;
-    if (c->cfg.dtype == SDTW_I8 && N > kI8MaxN) return SDTW_E_INVALID;
+    if (int_mode(c->cfg.dtype) && N > kI8MaxN) return SDTW_E_INVALID;
     return SDTW_OK;
 }
 
@@ -192,7 +206,7 @@ CkLayout ck_layout(int64_t M, int N, const FwdPlan& p)
 {
     CkLayout l;
     l.K = 8 * p.W;
-    l.fr_slot = sdtw::fr_slot_floats(M, N, p.W, p.P, p.RT);
+    l.fr_slot = sdtw::fr_slot_floats(M, N, p.W, p.P, p.RT, p.KS);
     l.ck_slot = sdtw::ck_slot_floats(M, N, l.K);
     l.per_q = l.fr_slot + l.ck_slot + M + 7;
     return l;
@@ -245,7 +259,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     if (p.smem > kMaxSmem) return SDTW_E_UNSUPPORTED;
     if (sdtw::fwd_total_steps(M, N, p.W, p.P, p.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
     if (p.persistent) p.grid = std::min(p.grid, nq);
-    else p.grid = nq;
+    else p.grid = plain_grid(c->cfg.dtype, nq);
     FwdArgs a{};
     a.ref = ref;
     a.M = M;
@@ -265,8 +279,17 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
         a.K = ck->K;
         a.ck_cost = ck->ck_cost;
         a.ck_end = ck->ck_end;
+        a.ck_stride = p.KS;
+        a.rebase_period = sdtw::ckpt_rebase_period(p.KS);
     } else {
         a.K = 1;
+        a.ck_stride = sdtw::kChunk;
+        // in a context that runs backwards, rebase like the checkpointing
+        // fill of this shape: a forward then returns the same costs whether
+        // or not it stores checkpoints
+        a.rebase_period = (c->cfg.flags & SDTW_FLAG_GRAD) && c->cfg.dtype == SDTW_F32
+                              ? sdtw::ckpt_rebase_period(default_fwd_plan(c, B, N, M, ragged, true).KS)
+                              : sdtw::kChunk;
     }
     a.status = c->d_status;
     // the context's normalised copy holds max_total_query_len samples
@@ -404,7 +427,8 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     CallRange range("sdtw_create");
     if (!out || !cfg) return SDTW_E_INVALID;
     *out = nullptr;
-    if (cfg->dtype != SDTW_F32 && cfg->dtype != SDTW_I8) return SDTW_E_INVALID;
+    if (cfg->dtype != SDTW_F32 && cfg->dtype != SDTW_I8 && cfg->dtype != SDTW_U8 && cfg->dtype != SDTW_F16)
+        return SDTW_E_INVALID;
     if (cfg->max_ref_len < 1 || cfg->max_query_len < 1 || cfg->max_batch < 1 || cfg->max_total_query_len < 1)
         return SDTW_E_INVALID;
     if (cfg->max_ref_len > INT_MAX / 2) return SDTW_E_INVALID;
@@ -413,10 +437,13 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_ZNORM_QUERIES) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
-    if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0) return SDTW_E_INVALID;
-    if (cfg->ckpt_stride != 0 && cfg->ckpt_stride != sdtw::kChunk) return SDTW_E_UNSUPPORTED;
+    if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
+    if (cfg->ckpt_stride != 0 && !sdtw::ckpt_stride_supported(cfg->ckpt_stride)) return SDTW_E_UNSUPPORTED;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
-    if (cfg->dtype == SDTW_I8 && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
+    if (int_mode(cfg->dtype) && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
+    // the longest query any forward plan can stage in shared memory (one warp,
+    // the smallest ring): beyond it every call would fail
+    if (sdtw::fwd_smem_bytes(cfg->dtype, cfg->max_query_len, 1, 8, 4) > kMaxSmem) return SDTW_E_UNSUPPORTED;
 
     sdtw_ctx* c = new (std::nothrow) sdtw_ctx();
     if (!c) return SDTW_E_NOMEM;
@@ -464,6 +491,7 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
     CallRange range("sdtw_forward");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
+    if (offsets && ctx->cfg.dtype == SDTW_F16) return SDTW_E_UNSUPPORTED;  // binary16 pairs: uniform batches
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
     if (B == 0) return SDTW_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -485,6 +513,7 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
             ctx->key.W = cp.W;
             ctx->key.P = cp.P;
             ctx->key.RT = cp.RT;
+            ctx->key.KS = cp.KS;
             ctx->key.valid = true;
         }
         return s;
@@ -523,6 +552,8 @@ cudaError_t launch_bwd(sdtw_ctx* ctx, const FwdPlan& p, const CkPtrs& ck, const 
     a.W = p.W;
     a.P = p.P;
     a.RT = p.RT;
+    a.KS = p.KS;
+    a.rebase_period = sdtw::ckpt_rebase_period(p.KS);
     a.gyq = ck.gyq;
     a.span = ck.span;
     a.status = ctx->d_status;
@@ -550,9 +581,10 @@ static sdtw_status run_backward(sdtw_ctx* ctx, const float* ref, int64_t M, cons
         p.W = ctx->key.W;
         p.P = ctx->key.P;
         p.RT = ctx->key.RT;
+        p.KS = ctx->key.KS;
     }
     if (!sdtw::bwd_width_supported(p.W)) return SDTW_E_UNSUPPORTED;
-    if (sdtw::bwd_smem_bytes(N, p.W, p.RT) > kMaxSmem) return SDTW_E_UNSUPPORTED;
+    if (sdtw::bwd_smem_bytes(N, p.W, p.RT, p.KS) > kMaxSmem) return SDTW_E_UNSUPPORTED;
     const CkLayout l = ck_layout(M, N, p);
     const int64_t cap = chunk_capacity(ctx, l);
     if (cap < 1) return SDTW_E_NOMEM;
@@ -619,6 +651,7 @@ sdtw_status sdtw_forward_host(sdtw_ctx* ctx, const void* ref, int64_t M, const v
     CallRange range("sdtw_forward_host");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
+    if (offsets && ctx->cfg.dtype == SDTW_F16) return SDTW_E_UNSUPPORTED;
     if (B == 0) return SDTW_OK;
     const int64_t total = offsets ? offsets[B] : static_cast<int64_t>(B) * N;
     if (total < 0 || total > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
@@ -717,6 +750,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     CallRange range("sdtw_autotune");
     sdtw_status s = check_common(ctx, ref, M, queries, B, N, cost, end);
     if (s != SDTW_OK) return s;
+    if (offsets && ctx->cfg.dtype == SDTW_F16) return SDTW_E_UNSUPPORTED;
     if (B == 0) return SDTW_E_INVALID;
     if (!offsets && static_cast<int64_t>(B) * N > ctx->cfg.max_total_query_len) return SDTW_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -750,10 +784,18 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
         return SDTW_E_CUDA;
     }
     float best_ms = 1e30f;
-    int best_w = 0, best_p = 0, best_rt = 0;
+    int best_w = 0, best_p = 0, best_rt = 0, best_ks = 0;
     const int Ws[] = {8, 16, 20, 24, 28, 32};
     const int Ps[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
     const int RTs[] = {2, 4};
+    // the checkpoint stride is an axis only when checkpoints are stored (and
+    // the caller did not fix it); a stride whose checkpoints do not fit the
+    // arena under the memory cap is skipped like any other plan
+    std::vector<int> KSs;
+    if (!ckpt) KSs.push_back(kDefaultStride);
+    else if (ctx->cfg.ckpt_stride > 0) KSs.push_back(ctx->cfg.ckpt_stride);
+    else KSs.assign(std::begin(kStrides), std::end(kStrides));
+    for (int KS : KSs) {
     for (int RT : RTs) {
         for (int W : Ws) {
             for (int P : Ps) {
@@ -762,6 +804,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 p.W = W;
                 p.P = P;
                 p.RT = RT;
+                p.KS = KS;
                 p.block = 32 * P;
                 p.smem = sdtw::fwd_smem_bytes(ctx->cfg.dtype, N, P, W, RT);
                 if (p.smem > kMaxSmem) continue;
@@ -769,11 +812,11 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 if (ckpt && B > chunk_capacity(ctx, l)) continue;
                 const CkPtrs ck = ckpt ? carve(ctx, l, B, M) : CkPtrs{};
                 const bool with_bwd = t_gc && sdtw::bwd_width_supported(W) &&
-                                      sdtw::bwd_smem_bytes(N, W, RT) <= kMaxSmem;
+                                      sdtw::bwd_smem_bytes(N, W, RT, KS) <= kMaxSmem;
                 if (t_gc && !with_bwd) continue;  // a plan the backward cannot use
                 const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
                 if (per_sm <= 0) continue;
-                p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : B;
+                p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : plain_grid(ctx->cfg.dtype, B);
                 // one untimed run, then the best of two timed runs
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
@@ -809,9 +852,11 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                     best_w = W;
                     best_p = P;
                     best_rt = RT;
+                    best_ks = KS;
                 }
             }
         }
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -819,7 +864,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     free_scratch();
     if (best_w == 0) return SDTW_E_UNSUPPORTED;
     ctx->tuned[TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0}] =
-        std::make_tuple(best_w, best_p, best_rt);
+        std::make_tuple(best_w, best_p, best_rt, best_ks);
     ctx->key.valid = false;
     if (plan) return sdtw_get_plan(ctx, B, N, M, ragged ? 1 : 0, 0, plan);
     return SDTW_OK;
@@ -837,10 +882,10 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
     plan->warps_per_query = p.P;
     plan->ctas_per_query = 1;
     plan->persistent = p.persistent ? 1 : 0;
-    plan->grid = p.persistent ? p.grid : B;
+    plan->grid = p.persistent ? p.grid : plain_grid(ctx->cfg.dtype, B);
     plan->block = p.block;
-    plan->smem_bytes = p.smem;
-    plan->ckpt_stride = ckpt ? sdtw::kChunk : 0;
+    plan->smem_bytes = static_cast<int32_t>(std::min<int64_t>(p.smem, INT32_MAX));
+    plan->ckpt_stride = ckpt ? p.KS : 0;
     plan->ckpt_cols = ckpt ? 8 * p.W : 0;
     plan->tuned = ctx->tuned.count(TuneKey{ctx->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0})
                       ? 1

@@ -8,16 +8,17 @@
 //   d cost / d y_j = sum over the path's cells in column j of -2 (x_i - y_j).
 //
 // The n x M matrix is never stored.  The checkpointing forward left, at the
-// end of every chunk of kChunk steps, its wavefront (each thread's latest
+// start of every KS-th step (KS = 16, 32 or 64), its wavefront (each thread's latest
 // row, the right-hand cells of its tile's other rows, its diagonal input and
-// its integer base: an anti-diagonal staircase of rows, stored before the
-// next chunk's rebase, which is redone here), and the left inputs of every
+// its integer base: an anti-diagonal staircase of rows, stored before a
+// rebase due at that step, which is redone here), and the left inputs of every
 // strip that starts a K-column window (K = 8 W).  The cells that the
-// eight strips of one window computed during one chunk form a band, a
-// parallelogram (each strip one tile higher than its left neighbour).  The
+// eight strips of one window computed during the KS steps after one
+// checkpoint form a band, a parallelogram (each strip one tile higher than
+// its left neighbour).  The
 // walk proceeds band by band, one warp per query:
 //   * the warp recomputes the band's rows down to the current cell from the
-//     chunk's wavefront and the window's boundary column, with the forward's
+//     checkpointed wavefront and the window's boundary column, with the forward's
 //     own operations in the forward's own bases (four lanes per strip, W/4
 //     columns each; each step a lane advances RS rows, RS dependency chains,
 //     one step behind lane l-1), so every value is the
@@ -133,10 +134,11 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* xs = reinterpret_cast<float*>(smem_raw);  // [N] query samples
     float* ys = xs + N;                              // [KW] reference samples of the window
-    float* lcol = ys + KW;                           // [RT*kChunk] the window's boundary column
-    float* gqs = lcol + RT * kChunk;                 // [N] the query's gradient, summed band by band
+    const int KS = a.KS;                             // a band's height in forward steps
+    float* lcol = ys + KW;                           // [RT*KS] the window's boundary column
+    float* gqs = lcol + RT * KS;                     // [N] the query's gradient, summed band by band
     float* rowpart = gqs + N;                        // [band rows][33] per-lane shares of each row's gradient
-    DW* dirs = reinterpret_cast<DW*>(rowpart + (RT * kChunk + 7 * RT) * 33);  // [RS*steps][32] walk-back choices
+    DW* dirs = reinterpret_cast<DW*>(rowpart + (RT * KS + 7 * RT) * 33);  // [RS*steps][32] walk-back choices
 
     int64_t start;
     int n;
@@ -205,22 +207,22 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     // every band holds at least the walk's current cell, so a path of at most
     // n + M cells needs at most that many bands
     for (int64_t guard = 0; !done; ++guard) {
-        // ---- the band holding (wi, wj): window b, chunk c
+        // ---- the band holding (wi, wj): window b, checkpoint c
         const int b = wj / KW, c0 = b * KW, s = c0 / S;
         const int tau0 = (c0 - s * S) / W;   // forward thread of the window's first strip
         const int lag0 = (tau0 >> 5) * (32 + kChunk) + (tau0 & 31);  // strips of a window share a warp
         const int dj = (wj - c0) / W;
-        const int c = (wi / RT + lag0 + dj + s * Pp) / kChunk;
-        const int ps0 = c * kChunk - lag0 - s * Pp;  // strip 0's tile at the chunk start
+        const int c = (wi / RT + lag0 + dj + s * Pp) / KS;  // the checkpoint the band starts from
+        const int ps0 = c * KS - lag0 - s * Pp;  // strip 0's tile at the band's first step
         const int rtop = RT * (ps0 - 7);             // the top of the band's rightmost strip
         const int ps = ps0 - d;                      // this lane's strip
         const int rf = RT * max(0, ps);              // its rows in the band: [rf, re)
-        const int re = min(n, RT * min(nt, ps + kChunk));
+        const int re = min(n, RT * min(nt, ps + KS));
         const int rf_left = RT * max(0, ps + 1);     // the strip on the left starts here
         const int rf0 = RT * max(0, ps0);
-        const int re0 = min(min(n, RT * min(nt, ps0 + kChunk)), wi + 1);
+        const int re0 = min(min(n, RT * min(nt, ps0 + KS)), wi + 1);
         if (guard > static_cast<int64_t>(n) + M || wi < RT * max(0, ps0 - dj) ||
-            wi >= min(n, RT * min(nt, ps0 - dj + kChunk))) {
+            wi >= min(n, RT * min(nt, ps0 - dj + KS))) {
             // the current cell is not in its band: report and give up on this query
             if (lane == 0) {
                 atomicOr(a.status, kStatusReplay);
@@ -235,17 +237,19 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         if (b > 0)
             for (int k = lane; k < re0 - rf0; k += 32) lcol[k] = ckq[static_cast<int64_t>(b - 1) * ck_rows(N) + rf0 + k];
 
-        // ---- the lane's starting state: the chunk's wavefront, or the virtual
-        // zero row -1 for a strip that starts its sweep inside the chunk
+        // ---- the lane's starting state: the checkpointed wavefront, or the virtual
+        // zero row -1 for a strip that starts its sweep inside the band
         const float* frc = frq + static_cast<int64_t>(c) * L * (W + erec);
         const int tau = tau0 + d;
         auto fr_at = [&](int j, int th) { return frc[((j >> 2) * L + th) * 4 + (j & 3)]; };
         auto rec_at = [&](int e, int th) { return frc[(((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]; };
-        // the forward stored its state before the chunk's rebase: redo it
-        // (new base: the integer part of the strip's first column)
+        // the forward stored its state before a rebase due at the band's
+        // first step: redo it (new base: the integer part of the strip's first
+        // column); a checkpoint between rebases is already in its base
+        const bool redo = (c * KS) % a.rebase_period == 0;
         auto rebase = [&](int th, float& bn, float& dl) {
             const float b0 = rec_at(RT == 2 ? 2 : 4, th);
-            bn = floorf(b0 + fr_at(0, th));
+            bn = redo ? floorf(b0 + fr_at(0, th)) : b0;
             dl = bn - b0;
         };
         float D[WB], y[WB];
@@ -262,11 +266,10 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         }
         // the first lane of strips 1..7: the left strip's last tile before the
         // band (rows RT*ps .. RT*ps + RT-1, its right-hand cells) and its base
-        float e[RT], dd = 0.f;
+        float e[RT], Bsrc = 0.f;
 #pragma unroll
         for (int h = 0; h < RT; ++h) e[h] = 0.f;
         if (sub == 0 && d >= 1) {
-            float Bsrc = 0.f;
             if (ps + 1 >= 1 && ps + 1 <= nt) {
                 float dl;
                 rebase(tau - 1, Bsrc, dl);
@@ -274,7 +277,6 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
                 for (int h = 0; h < RT - 1; ++h) e[h] = rec_at(h, tau - 1) - dl;
                 e[RT - 1] = fr_at(W - 1, tau - 1) - dl;
             }
-            dd = Bsrc - Bl;
         }
         __syncwarp();
 #pragma unroll
@@ -298,20 +300,33 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
         // earliest of those (the rightmost strip's top is up to 7 tiles above
         // the others', so the first steps are often empty)
         const int sg0 = __reduce_min_sync(0xffffffffu, static_cast<unsigned>(rf < hi ? (rf - rtop) / RS + lane : steps));
+        // the forward's rebases to a left input far below the base, replayed:
+        // a strip's first lane decides at each tile's first row (the left input
+        // of that row, as the forward converted it) and the strip's other
+        // lanes follow the base their left lane's values arrive in
+        float Btile = Bl, dltile = 0.f;  // first lanes: the base the tile's inputs were converted into, and the shift
         for (int sg = sg0; sg < steps; ++sg) {
             float recv[RS];
 #pragma unroll
             for (int h = 0; h < RS; ++h) recv[h] = __shfl_up_sync(0xffffffffu, last[h], 1);
+            const float Brecv = __shfl_up_sync(0xffffffffu, Bl, 1);  // the base of the values received
             const int r = rtop + RS * (sg - lane);
             if (r >= rf && r < hi) {
                 const int v = min(RS, hi - r);  // valid rows of this step
-                // left inputs without divergent branches: a strip's first lane
-                // converts its left strip's values (from the left lane, or the
-                // stored record for the strip's first tile) into its own base
-                // (dd is 0 for the other lanes, whose values share the base), the
-                // window's first strip reads the stored boundary column
+                // left inputs: a strip's first lane converts its left strip's
+                // values (from the left lane, or the stored record for the
+                // strip's first tile) into its own base as the forward did,
+                // the window's first strip reads the stored boundary column;
+                // the other lanes take their left lane's values as they are
                 const bool from_rec = sub == 0 && r < rf_left;  // a strip's first tile, first lane
+                const bool tile_start = (r & (RT - 1)) == 0;
                 const int eo = r - rf;                           // ... and the step's rows in it
+                // a strip's other lanes follow the base their left lane's values
+                // arrive in (the first lane rebased at these rows); the first
+                // lane's own rebase is decided below, once its inputs are converted
+                const float follow = sub != 0 ? Brecv - Bl : 0.f;
+                if (tile_start) Btile = Bl;
+                const float dconv = (from_rec ? Bsrc : Brecv) - Btile;
                 float l[RS], x[RS];
 #pragma unroll
                 for (int h = 0; h < RS; ++h) {
@@ -319,12 +334,29 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
 #pragma unroll
                     for (int o = RS; o < RT; o += RS)
                         if (eo == o) ev = e[h + o];
-                    float lv = (from_rec ? ev : recv[h]) + dd;
+                    float lv = recv[h];
+                    if (sub == 0) lv = (from_rec ? ev : recv[h]) + dconv;
                     if (d == 0 && sub == 0) lv = INF;
                     if (d == 0 && sub == 0 && b > 0 && h < v) lv = lcol[r + h - rf0];
                     l[h] = lv;
                     x[h] = h < v ? xs[r + h] : 0.f;
                 }
+                // the first lane's rebase at a tile's first row, as the forward
+                // decides it; the tile's later rows take the same shift.  The
+                // shift is applied without a branch: a lane without one shifts
+                // by 0, which changes no value (x - 0 == x, signed zeros
+                // included), and a divergent branch here costs more than the
+                // subtractions in this latency-bound loop
+                const bool trig = sub == 0 && tile_start && l[0] < -kRebaseBelow;
+                const float dlt = trig ? floorf(Bl + l[0]) - Bl : 0.f;
+                if (sub == 0 && tile_start) dltile = dlt;
+                const float sh = sub != 0 ? follow : dlt;
+#pragma unroll
+                for (int k = 0; k < WB; ++k) D[k] -= sh;
+                dg -= sh;
+                Bl += sh;
+#pragma unroll
+                for (int h = 0; h < RS; ++h) l[h] -= dltile;
                 const float dg_next = l[RS - 1];
                 uint32_t nd[RS], nu[RS];
                 if (first)
@@ -461,7 +493,9 @@ __global__ void grad_ref_reduce_kernel(const float* __restrict__ gyq, const int6
 template <int WB>
 cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 {
-    const int smem = bwd_smem_bytes(a.N, 4 * WB, a.RT);
+    const int64_t smem64 = bwd_smem_bytes(a.N, 4 * WB, a.RT, a.KS);
+    if (smem64 < 0 || smem64 > kMaxSmemBytes) return cudaErrorInvalidValue;
+    const int smem = static_cast<int>(smem64);
     auto k = a.RT == 2 ? bwd_band_kernel<WB, 2, rows_per_step(2)> : bwd_band_kernel<WB, 4, rows_per_step(4)>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -475,23 +509,26 @@ cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
 
 bool bwd_width_supported(int W) { return W == 8 || W == 16 || W == 20 || W == 24 || W == 28 || W == 32; }
 
-int bwd_smem_bytes(int N, int W, int RT)
+int64_t bwd_smem_bytes(int64_t N, int W, int RT, int KS)
 {
     // query samples and gradient, the window's samples and boundary column,
     // the lanes' shares of the band's row gradients (33 floats per row), and
-    // the choices of up to RT*kChunk + 7*RT + 32*RS rows of 32 lanes (W/2 bits
+    // the choices of up to RT*KS + 7*RT + 32*RS rows of 32 lanes (W/2 bits
     // each): the band's rows below the top of its rightmost strip, and the
     // lag of RS rows per lane
-    const int word = W <= 16 ? 1 : 2;
-    const int RS = rows_per_step(RT);
-    return 4 * (2 * N + 8 * W + RT * kChunk) + 4 * (RT * kChunk + 7 * RT) * 33 +
-           (RT * kChunk + 7 * RT + 32 * RS) * 32 * word;
+    const int64_t word = W <= 16 ? 1 : 2;
+    const int64_t RS = rows_per_step(RT);
+    const int64_t rows = static_cast<int64_t>(RT) * KS;
+    if (N < 0) N = 0;
+    return 4 * (2 * N + 8 * W + rows) + 4 * (rows + 7 * RT) * 33 + (rows + 7 * RT + 32 * RS) * 32 * word;
 }
 
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)
 {
     if (a.B <= 0) return cudaSuccess;
-    if (a.K != 8 * a.W || (a.RT != 2 && a.RT != 4)) return cudaErrorInvalidValue;
+    if (a.K != 8 * a.W || (a.RT != 2 && a.RT != 4) || !ckpt_stride_supported(a.KS) ||
+        a.rebase_period != ckpt_rebase_period(a.KS))
+        return cudaErrorInvalidValue;
     switch (a.W) {
     case 8: return launch_walk_wb<2>(a, s);
     case 16: return launch_walk_wb<4>(a, s);

@@ -67,6 +67,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "sdtw_cell.cuh"
 #include "sdtw_internal.h"
@@ -91,17 +92,30 @@ template <>
 struct VecOf<int32_t, 2> { using T = int2; };
 template <>
 struct VecOf<int32_t, 4> { using T = int4; };
+template <>
+struct VecOf<__half2, 2> { using T = uint2; };
+template <>
+struct VecOf<__half2, 4> { using T = uint4; };
 
 // the RT query samples of tile p (xs is 16-byte aligned and zero padded)
 template <int RT, typename V>
 __device__ __forceinline__ void load_x(const V* xs, int p, V (&x)[RT])
 {
     const auto v = reinterpret_cast<const typename VecOf<V, RT>::T*>(xs)[p];
-    x[0] = v.x;
-    x[1] = v.y;
-    if constexpr (RT == 4) {
-        x[2] = v.z;
-        x[3] = v.w;
+    if constexpr (std::is_same<V, __half2>::value) {
+        x[0] = Mode<__half>::from_bits(v.x);
+        x[1] = Mode<__half>::from_bits(v.y);
+        if constexpr (RT == 4) {
+            x[2] = Mode<__half>::from_bits(v.z);
+            x[3] = Mode<__half>::from_bits(v.w);
+        }
+    } else {
+        x[0] = v.x;
+        x[1] = v.y;
+        if constexpr (RT == 4) {
+            x[2] = v.z;
+            x[3] = v.w;
+        }
     }
 }
 
@@ -117,7 +131,8 @@ template <typename Md, int W, int RT, bool BOT>
 __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md::V (&A)[RT - 1][W],
                                           const typename Md::V (&y)[W], const typename Md::V (&x)[RT],
                                           typename Md::V diag, const typename Md::V (&left)[RT], int bot_row,
-                                          float B, int base, int M, typename Md::V& best, int& best_col)
+                                          float B, int base, int M, typename Md::V& best,
+                                          typename Md::Col& best_col)
 {
     using V = typename Md::V;
 #pragma unroll
@@ -147,11 +162,15 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
                 A[rr][j] = nv;
             if constexpr (BOT) {
                 if (rr == bot_row) {
-                    V v = nv;
-                    if constexpr (Md::kRebase) v = nv + B;
-                    if (base + j < M && v < best) {
-                        best = v;
-                        best_col = base + j;
+                    if constexpr (Md::kPair) {
+                        if (base + j < M) Md::bot_update(nv, base + j, best, best_col);
+                    } else {
+                        V v = nv;
+                        if constexpr (Md::kRebase) v = nv + B;
+                        if (base + j < M && v < best) {
+                            best = v;
+                            best_col = base + j;
+                        }
                     }
                 }
             }
@@ -164,18 +183,50 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
 // of exact ties), as the in-tile update of tile_step does.
 template <typename Md, int W>
 __device__ __forceinline__ void bottom_min_prev(const typename Md::V (&prev)[W], float B, int base, int M,
-                                                typename Md::V& best, int& best_col)
+                                                typename Md::V& best, typename Md::Col& best_col)
 {
     using V = typename Md::V;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        V v = prev[j];
-        if constexpr (Md::kRebase) v = v + B;
-        if (base + j < M && v < best) {
-            best = v;
-            best_col = base + j;
+        if constexpr (Md::kPair) {
+            if (base + j < M) Md::bot_update(prev[j], base + j, best, best_col);
+        } else {
+            V v = prev[j];
+            if constexpr (Md::kRebase) v = v + B;
+            if (base + j < M && v < best) {
+                best = v;
+                best_col = base + j;
+            }
         }
     }
+}
+
+// FP32 mode: a left input far below the strip's base.  A horizontal run of
+// the path entering from a cheaper strip carries values far below the bases
+// the strips it crosses took from their own cells, and every cell of the run
+// would then round at the scale of that gap.  When the tile's first-row left
+// input lies more than kRebaseBelow under the base, the strip is rebased to
+// it (an integer base again, so the shift is an integer) before the tile:
+// the previous row, the diagonal input and the tile's left inputs move with
+// it.  The decision uses the first row only, which the backward's replay of
+// the band also has when it recomputes that row.
+template <bool VOTE, int W, int RT>
+__device__ __forceinline__ bool rebase_to_left(float (&prev)[W], float& diag, float (&left)[RT], float& B)
+{
+    // decided per lane; with VOTE (all 32 lanes present) applied under a warp
+    // vote, lanes that keep their base shifting by 0, so that the common step
+    // (no lane rebases) takes no divergent branch
+    const bool low = left[0] < -kRebaseBelow;
+    if (VOTE ? !__any_sync(0xffffffffu, low) : !low) return false;
+    const float bn = low ? floorf(B + left[0]) : B;
+    const float dl = bn - B;
+#pragma unroll
+    for (int k = 0; k < W; ++k) prev[k] -= dl;
+    diag -= dl;
+#pragma unroll
+    for (int rr = 0; rr < RT; ++rr) left[rr] -= dl;
+    B = bn;
+    return true;
 }
 
 // The RT left inputs of a tile as one vector store (the destination is
@@ -250,23 +301,41 @@ fwd_chain_kernel(const FwdArgs a)
             if (threadIdx.x == 0) s_query = atomicAdd(a.queue, 1);
             __syncthreads();
             q = s_query;
-            if (q >= a.B) break;
-            q = a.order ? a.order[q] : a.q0 + q;
+            if constexpr (Md::kPair) {
+                // binary16 pairs (uniform batches): work item q is queries 2q, 2q+1
+                if (2 * q >= a.B) break;
+                q = a.q0 + 2 * q;
+            } else {
+                if (q >= a.B) break;
+                q = a.order ? a.order[q] : a.q0 + q;
+            }
         } else {
             if (it > 0) break;
-            q = a.q0 + blockIdx.x;
+            q = a.q0 + (Md::kPair ? 2 : 1) * static_cast<int>(blockIdx.x);
         }
 
         int64_t start;
         int n;
-        if (a.offsets) {
+        int qb = q;  // binary16 pairs: the query in the high halves (the last pair of an odd batch repeats q)
+        if constexpr (Md::kPair) {
+            // uniform batches only: the CTA's two queries, both N long
+            qb = min(q + 1, a.q0 + a.B - 1);
+            start = static_cast<int64_t>(q) * N;
+            n = N;
+        } else if (a.offsets) {
             // 0 <= offsets[q] <= offsets[q+1] <= offsets[B]: the query lies inside the batch
             start = a.offsets[q];
             const int64_t stop = a.offsets[q + 1];
             const int64_t len = stop - start;
             bool bad = start < 0 || len < 0 || len > N || stop > a.offsets[a.B_total] || (a.q_limit > 0 && stop > a.q_limit);
             if (bad) {
-                if (threadIdx.x == 0) atomicOr(a.status, kStatusBadLength);
+                // flagged, and the outputs get the empty query's values, so that
+                // no caller reads a stale cost or end for it
+                if (threadIdx.x == 0) {
+                    atomicOr(a.status, kStatusBadLength);
+                    static_cast<V*>(a.cost)[q] = Md::empty_cost();
+                    a.end[q] = -1;
+                }
                 __syncthreads();
                 continue;
             }
@@ -275,18 +344,26 @@ fwd_chain_kernel(const FwdArgs a)
             start = static_cast<int64_t>(q) * N;
             n = N;
         }
-        if (n == 0) {
-            if (threadIdx.x == 0) {
-                static_cast<V*>(a.cost)[q] = Md::empty_cost();
-                a.end[q] = -1;
+        if constexpr (!Md::kPair) {
+            if (n == 0) {
+                if (threadIdx.x == 0) {
+                    static_cast<V*>(a.cost)[q] = Md::empty_cost();
+                    a.end[q] = -1;
+                }
+                __syncthreads();
+                continue;
             }
-            __syncthreads();
-            continue;
         }
 
         const int nt = (n + RT - 1) / RT;  // tiles of rows per sweep
-        for (int i = threadIdx.x; i < nt * RT; i += blockDim.x)
-            xs[i] = i < n ? Md::widen(queries[start + i]) : Md::zero();  // dummy rows complete the last tile
+        if constexpr (Md::kPair) {
+            const int64_t startb = static_cast<int64_t>(qb) * N;
+            for (int i = threadIdx.x; i < nt * RT; i += blockDim.x)
+                xs[i] = i < n ? Md::pack(queries[start + i], queries[startb + i]) : Md::zero();
+        } else {
+            for (int i = threadIdx.x; i < nt * RT; i += blockDim.x)
+                xs[i] = i < n ? Md::widen(queries[start + i]) : Md::zero();  // dummy rows complete the last tile
+        }
         __syncthreads();
 
         const int lastt = nt - 1;                 // the tile holding row n-1
@@ -305,7 +382,11 @@ fwd_chain_kernel(const FwdArgs a)
         V diag = Md::zero();
         float B = 0.f;  // FP32 mode: this thread's base (absolute D = B + D')
         V best = INF;
-        int best_col = INT_MAX;
+        typename Md::Col best_col;
+        if constexpr (Md::kPair)
+            best_col = make_int2(INT_MAX, INT_MAX);
+        else
+            best_col = INT_MAX;
         int p = -lag;   // tile of this thread's strip in sweep s (negative: not started)
         int s = 0;      // sweep
         int base = threadIdx.x * W;  // first column of the strip in sweep s
@@ -314,8 +395,18 @@ fwd_chain_kernel(const FwdArgs a)
         float* frq = CKPT ? a.fr + static_cast<int64_t>(q - a.q0) * a.fr_slot : nullptr;
         float* ck = nullptr;
 
+        // checkpointing: the wavefront is stored every ks steps (16, 32 or 64),
+        // so a chunk runs as segments of seg steps with a store between them
+        const int ks = CKPT ? a.ck_stride : kChunk;
+        const int seg = CKPT ? min(ks, kChunk) : kChunk;
         for (int t0 = 0; t0 < total; t0 += kChunk) {
-            if constexpr (Md::kRebase) {
+            // rebase at the start of every rebase period (a whole number of
+            // chunks: one, or two with 64-step checkpoints, so that the
+            // checkpoints always fall on rebase boundaries or between them;
+            // a plain fill in a context that keeps checkpoints rebases like
+            // its checkpointing fill, so that both return the same costs)
+            const bool do_rebase = (t0 & (a.rebase_period - 1)) == 0;
+            if constexpr (Md::kRebase) if (do_rebase) {
                 // new base: the integer part of the strip's first column; bases
                 // are integers (exact below 2^24), so base differences, the
                 // shift and every conversion between threads add no rounding
@@ -337,135 +428,54 @@ fwd_chain_kernel(const FwdArgs a)
                 const int sw = gmin / Pp;
                 fast = gmax / Pp == sw && sw < nsw && gmin - sw * Pp >= 1 && gmax - sw * Pp <= lastt - 1;
             }
-            if (fast) {
-                float dconv = 0.f;  // base difference to the left neighbour, fixed for the chunk
-                if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
+            for (int ub = 0; ub < kChunk; ub += seg) {
+                const int ue = ub + seg;
+                if (fast) {
+                    // base difference to the left neighbour: fixed between rebases
+                    float dconv = 0.f;
+                    if constexpr (Md::kRebase) dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
 #pragma unroll 1
-                for (int u = 0; u < kChunk; ++u) {
-                    const int t = t0 + u;
-                    V recv[RT];
+                    for (int u = ub; u < ue; ++u) {
+                        const int t = t0 + u;
+                        V recv[RT];
 #pragma unroll
-                    for (int rr = 0; rr < RT; ++rr)
-                        recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
-                    float dd = dconv;
-                    if (lane == 0) {
-                        if (warp > 0) {
-                            const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
+                        for (int rr = 0; rr < RT; ++rr)
+                            recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
+                        float dd = dconv;
+                        if (lane == 0) {
+                            if (warp > 0) {
+                                const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
 #pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
-                            dd = e.b - B;
-                        } else if (s > 0) {
-                            const E e = colbuf[p];
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
+                                dd = e.b - B;
+                            } else if (s > 0) {
+                                const E e = colbuf[p];
 #pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
-                            dd = e.b - B;
-                        } else {
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
+                                dd = e.b - B;
+                            } else {
 #pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
-                            dd = 0.f;
-                        }
-                    }
-                    V left[RT];
-#pragma unroll
-                    for (int rr = 0; rr < RT; ++rr) {
-                        left[rr] = recv[rr];
-                        if constexpr (Md::kRebase) left[rr] = recv[rr] + dd;
-                    }
-                    V x[RT];
-                    load_x<RT>(xs, p, x);
-                    tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
-                    diag = left[RT - 1];
-                    if (lane == 31) {
-                        E e;
-#pragma unroll
-                        for (int rr = 0; rr < RT; ++rr) e.v[rr] = rr < RT - 1 ? A[rr][W - 1] : prev[W - 1];
-                        e.b = B;
-                        if (warp < P - 1)
-                            ring_out[t & (kRing - 1)] = e;
-                        else
-                            colbuf[p] = e;
-                    }
-                    if constexpr (CKPT) {
-                        if (ck) store_rows<RT>(ck + RT * p, left);
-                    }
-                    ++p;
-                    // a one-warp chain reads and rewrites the column buffer less than
-                    // a chunk apart: order those accesses within the warp
-                    if (P == 1) __syncwarp();
-                }
-            } else {
-#pragma unroll 1
-                for (int u = 0; u < kChunk; ++u) {
-                    const int t = t0 + u;
-                    V recv[RT];
-#pragma unroll
-                    for (int rr = 0; rr < RT; ++rr)
-                        recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
-                    float rb = 0.f;
-                    if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
-                    const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(nt) && s < nsw;
-                    if (lane == 0) {
-                        if (warp > 0) {
-                            const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
-#pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
-                            rb = e.b;
-                        } else if (act && s > 0) {
-                            const E e = colbuf[p];
-#pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
-                            rb = e.b;
-                        } else {
-#pragma unroll
-                            for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
-                            rb = 0.f;
-                        }
-                    }
-                    if (act) {
-                        if (p == 0) {
-                            // new sweep: load the strip's reference samples; the
-                            // previous row is the virtual all-zero row -1
-                            base = s * S + threadIdx.x * W;
-#pragma unroll
-                            for (int k = 0; k < W; ++k) {
-                                const int col = base + k;
-                                y[k] = col < M ? Md::widen(ref[col]) : Md::zero();
-                                prev[k] = Md::zero();
-                            }
-                            diag = Md::zero();
-                            B = 0.f;
-                            if constexpr (CKPT) {
-                                // a strip starting a K-column window (not the first)
-                                // keeps its left inputs for the backward
-                                ck = nullptr;
-                                if (base % a.K == 0 && base > 0 && base < M)
-                                    ck = a.colck + static_cast<int64_t>(q - a.q0) * a.ck_slot +
-                                         static_cast<int64_t>(base / a.K - 1) * ck_rows(N);
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
+                                dd = 0.f;
                             }
                         }
                         V left[RT];
 #pragma unroll
                         for (int rr = 0; rr < RT; ++rr) {
                             left[rr] = recv[rr];
-                            if constexpr (Md::kRebase) left[rr] = recv[rr] + (rb - B);  // into this thread's base
+                            if constexpr (Md::kRebase) left[rr] = recv[rr] + dd;
+                        }
+                        if constexpr (CKPT) {
+                            if (ck) store_rows<RT>(ck + RT * p, left);  // as converted, before any shift
+                        }
+                        if constexpr (Md::kRebase) {
+                            // a lane that rebased changes its own and its right neighbour's conversion
+                            if (rebase_to_left<true, W, RT>(prev, diag, left, B))
+                                dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
                         }
                         V x[RT];
                         load_x<RT>(xs, p, x);
-                        if (bot == RT - 1) {
-                            // the query's last row is a tile's last row (RT divides n):
-                            // the plain tile, then the minimum over that row for the one
-                            // lane that holds it; updating the minimum inside every
-                            // cell of the tile measured 17-21% of the whole fill
-                            tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
-                            if (p == lastt) bottom_min_prev<Md, W>(prev, B, base, M, best, best_col);
-                        } else if (__any_sync(__activemask(), p == lastt)) {
-                            // the last row inside a tile: update the minimum in the cells,
-                            // only on the steps where some lane of the warp holds that tile
-                            tile_step<Md, W, RT, true>(prev, A, y, x, diag, left, p == lastt ? bot : -1, B, base, M,
-                                                       best, best_col);
-                        } else {
-                            tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
-                        }
+                        tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
                         diag = left[RT - 1];
                         if (lane == 31) {
                             E e;
@@ -477,40 +487,185 @@ fwd_chain_kernel(const FwdArgs a)
                             else
                                 colbuf[p] = e;
                         }
-                        if constexpr (CKPT) {
-                            if (ck) store_rows<RT>(ck + RT * p, left);  // padding rows fall in the padded slot
+                        ++p;
+                        // a one-warp chain reads and rewrites the column buffer less than
+                        // a chunk apart: order those accesses within the warp
+                        if (P == 1) __syncwarp();
+                    }
+                } else {
+#pragma unroll 1
+                    for (int u = ub; u < ue; ++u) {
+                        const int t = t0 + u;
+                        V recv[RT];
+#pragma unroll
+                        for (int rr = 0; rr < RT; ++rr)
+                            recv[rr] = __shfl_up_sync(0xffffffffu, rr < RT - 1 ? A[rr][W - 1] : prev[W - 1], 1);
+                        float rb = 0.f;
+                        if constexpr (Md::kRebase) rb = __shfl_up_sync(0xffffffffu, B, 1);
+                        const bool act = static_cast<unsigned>(p) < static_cast<unsigned>(nt) && s < nsw;
+                        if (lane == 0) {
+                            if (warp > 0) {
+                                const E e = ring_in[(t - kChunk - 1) & (kRing - 1)];
+#pragma unroll
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
+                                rb = e.b;
+                            } else if (act && s > 0) {
+                                const E e = colbuf[p];
+#pragma unroll
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = e.v[rr];
+                                rb = e.b;
+                            } else {
+#pragma unroll
+                                for (int rr = 0; rr < RT; ++rr) recv[rr] = INF;
+                                rb = 0.f;
+                            }
+                        }
+                        if (act) {
+                            if (p == 0) {
+                                // new sweep: load the strip's reference samples; the
+                                // previous row is the virtual all-zero row -1
+                                base = s * S + threadIdx.x * W;
+#pragma unroll
+                                for (int k = 0; k < W; ++k) {
+                                    const int col = base + k;
+                                    y[k] = col < M ? Md::widen(ref[col]) : Md::zero();
+                                    prev[k] = Md::zero();
+                                }
+                                diag = Md::zero();
+                                B = 0.f;
+                                if constexpr (CKPT) {
+                                    // a strip starting a K-column window (not the first)
+                                    // keeps its left inputs for the backward
+                                    ck = nullptr;
+                                    if (base % a.K == 0 && base > 0 && base < M)
+                                        ck = a.colck + static_cast<int64_t>(q - a.q0) * a.ck_slot +
+                                             static_cast<int64_t>(base / a.K - 1) * ck_rows(N);
+                                }
+                            }
+                            V left[RT];
+#pragma unroll
+                            for (int rr = 0; rr < RT; ++rr) {
+                                left[rr] = recv[rr];
+                                if constexpr (Md::kRebase) left[rr] = recv[rr] + (rb - B);  // into this thread's base
+                            }
+                            if constexpr (CKPT) {
+                                // as converted, before any shift; padding rows fall in the padded slot
+                                if (ck) store_rows<RT>(ck + RT * p, left);
+                            }
+                            if constexpr (Md::kRebase) rebase_to_left<false, W, RT>(prev, diag, left, B);
+                            V x[RT];
+                            load_x<RT>(xs, p, x);
+                            if (bot == RT - 1) {
+                                // the query's last row is a tile's last row (RT divides n):
+                                // the plain tile, then the minimum over that row for the one
+                                // lane that holds it; updating the minimum inside every
+                                // cell of the tile measured 17-21% of the whole fill
+                                tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
+                                if (p == lastt) bottom_min_prev<Md, W>(prev, B, base, M, best, best_col);
+                            } else if (__any_sync(__activemask(), p == lastt)) {
+                                // the last row inside a tile: update the minimum in the cells,
+                                // only on the steps where some lane of the warp holds that tile
+                                tile_step<Md, W, RT, true>(prev, A, y, x, diag, left, p == lastt ? bot : -1, B, base, M,
+                                                           best, best_col);
+                            } else {
+                                tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
+                            }
+                            diag = left[RT - 1];
+                            if (lane == 31) {
+                                E e;
+#pragma unroll
+                                for (int rr = 0; rr < RT; ++rr) e.v[rr] = rr < RT - 1 ? A[rr][W - 1] : prev[W - 1];
+                                e.b = B;
+                                if (warp < P - 1)
+                                    ring_out[t & (kRing - 1)] = e;
+                                else
+                                    colbuf[p] = e;
+                            }
+                        }
+                        if (++p == Pp) {
+                            p = 0;
+                            ++s;
+                        }
+                        if (P == 1) __syncwarp();
+                    }
+                }
+                if constexpr (CKPT) {
+                    // the wavefront as this segment leaves it (the state at the
+                    // start of step tend, before a rebase due there), if this thread
+                    // has computed a tile (p == 0 of a later sweep still holds the
+                    // previous sweep's last tile when the period has no idle steps)
+                    const int tend = t0 + ue;
+                    const int c1 = tend / ks;
+                    if (tend - c1 * ks == 0 && tend < total &&
+                        ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt))) {
+                        float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(c1) * L * (W + EREC)) +
+                                     threadIdx.x;
+#pragma unroll
+                        for (int k = 0; k < W / 4; ++k)
+                            __stcs(f4 + k * L, make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]));
+                        if constexpr (RT == 2) {
+                            __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], diag, B, 0.f));
+                        } else {
+                            __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag));
+                            __stcs(f4 + (W / 4 + 1) * L, make_float4(B, 0.f, 0.f, 0.f));
                         }
                     }
-                    if (++p == Pp) {
-                        p = 0;
-                        ++s;
-                    }
-                    if (P == 1) __syncwarp();
                 }
-            }
-            if constexpr (CKPT) {
-                // the wavefront as this chunk leaves it (the state at the start
-                // of the next chunk, before its rebase), if this thread has
-                // computed a tile (p == 0 of a later sweep still holds the
-                // previous sweep's last tile when the period has no idle steps)
-                const int c1 = t0 / kChunk + 1;
-                if (t0 + kChunk < total && ((p >= 1 && p <= nt && s < nsw) || (p == 0 && s >= 1 && Pp == nt))) {
-                    float4* f4 = reinterpret_cast<float4*>(frq + static_cast<int64_t>(c1) * L * (W + EREC)) +
-                                 threadIdx.x;
-#pragma unroll
-                    for (int k = 0; k < W / 4; ++k)
-                        __stcs(f4 + k * L, make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]));
-                    if constexpr (RT == 2) {
-                        __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], diag, B, 0.f));
-                    } else {
-                        __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag));
-                        __stcs(f4 + (W / 4 + 1) * L, make_float4(B, 0.f, 0.f, 0.f));
-                    }
-                }
-            }
+            }  // segments
             __syncthreads();
         }
 
+        if constexpr (Md::kPair) {
+            // each half's lexicographic (value, column) minimum over the CTA;
+            // a last row that overflowed to +inf everywhere ends at column 0,
+            // the smallest column attaining the minimum
+            float b0 = __low2float(best), b1 = __high2float(best);
+            int c0 = best_col.x, c1 = best_col.y;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float o0 = __shfl_down_sync(0xffffffffu, b0, off), o1 = __shfl_down_sync(0xffffffffu, b1, off);
+                const int k0 = __shfl_down_sync(0xffffffffu, c0, off), k1 = __shfl_down_sync(0xffffffffu, c1, off);
+                if (o0 < b0 || (o0 == b0 && k0 < c0)) {
+                    b0 = o0;
+                    c0 = k0;
+                }
+                if (o1 < b1 || (o1 == b1 && k1 < c1)) {
+                    b1 = o1;
+                    c1 = k1;
+                }
+            }
+            float* red_f = reinterpret_cast<float*>(red_v);  // [P] floats, then the columns [2P]
+            if (lane == 0) {
+                red_f[warp] = b0;
+                red_i[2 * warp] = c0;
+                red_i[2 * warp + 1] = c1;
+            }
+            __syncthreads();
+            float* red_f1 = reinterpret_cast<float*>(red_i + 2 * P);  // [P]
+            if (lane == 0) red_f1[warp] = b1;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float v0 = red_f[0], v1 = red_f1[0];
+                int e0 = red_i[0], e1 = red_i[1];
+                for (int w = 1; w < P; ++w) {
+                    if (red_f[w] < v0 || (red_f[w] == v0 && red_i[2 * w] < e0)) {
+                        v0 = red_f[w];
+                        e0 = red_i[2 * w];
+                    }
+                    if (red_f1[w] < v1 || (red_f1[w] == v1 && red_i[2 * w + 1] < e1)) {
+                        v1 = red_f1[w];
+                        e1 = red_i[2 * w + 1];
+                    }
+                }
+                static_cast<float*>(a.cost)[q] = v0;
+                a.end[q] = e0 == INT_MAX ? 0 : e0;
+                if (qb != q) {
+                    static_cast<float*>(a.cost)[qb] = v1;
+                    a.end[qb] = e1 == INT_MAX ? 0 : e1;
+                }
+            }
+            __syncthreads();
+        } else {
         // lexicographic (value, column) minimum over the CTA
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -543,22 +698,37 @@ fwd_chain_kernel(const FwdArgs a)
             }
         }
         __syncthreads();
+        }  // scalar modes
     }
 }
 
-// rank of each query by length, longest first (ties by index): order[rank] = q
-__global__ void order_by_length_kernel(const int64_t* __restrict__ offsets, int32_t B,
-                                       int32_t* __restrict__ order)
+// rank of each query by length, longest first (ties by index): order[rank] = q.
+// Every thread counts the queries ranked before its own; the lengths are
+// staged in shared memory a tile at a time, so each is read from global memory
+// once per CTA rather than once per thread (B^2 comparisons, on-chip).
+constexpr int kOrderThreads = 256;
+constexpr int kOrderTile = 2048;
+
+__global__ void __launch_bounds__(kOrderThreads) order_by_length_kernel(const int64_t* __restrict__ offsets, int32_t B,
+                                                                        int32_t* __restrict__ order)
 {
+    __shared__ int64_t lens[kOrderTile];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= B) return;
-    const int64_t lq = offsets[q + 1] - offsets[q];
+    const int64_t lq = q < B ? offsets[q + 1] - offsets[q] : 0;
     int rank = 0;
-    for (int p = 0; p < B; ++p) {
-        const int64_t lp = offsets[p + 1] - offsets[p];
-        rank += (lp > lq) || (lp == lq && p < q);
+    for (int p0 = 0; p0 < B; p0 += kOrderTile) {
+        const int np = min(kOrderTile, B - p0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < np; k += blockDim.x) lens[k] = offsets[p0 + k + 1] - offsets[p0 + k];
+        __syncthreads();
+        if (q < B) {
+            for (int k = 0; k < np; ++k) {
+                const int64_t lp = lens[k];
+                rank += (lp > lq) || (lp == lq && p0 + k < q);
+            }
+        }
     }
-    order[rank] = q;
+    if (q < B) order[rank] = q;
 }
 
 template <typename Tin, int W, int RT, bool CKPT>
@@ -566,19 +736,26 @@ struct Inst {
     static cudaError_t launch(const FwdPlan& plan, const FwdArgs& a, cudaStream_t s)
     {
         auto k = fwd_chain_kernel<Tin, W, RT, CKPT>;
-        if (plan.smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+        if (plan.smem < 0 || plan.smem > kMaxSmemBytes) return cudaErrorInvalidValue;
+        const int smem = static_cast<int>(plan.smem);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
         }
-        k<<<plan.grid, plan.block, plan.smem, s>>>(a);
+        k<<<plan.grid, plan.block, smem, s>>>(a);
         return cudaGetLastError();
     }
-    static int occupancy(int block, int smem)
+    static int occupancy(int block, int64_t smem64)
     {
+        if (smem64 < 0 || smem64 > kMaxSmemBytes) return 0;
+        const int smem = static_cast<int>(smem64);
         int n = 0;
         auto k = fwd_chain_kernel<Tin, W, RT, CKPT>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
         return n;
     }
 };
@@ -603,6 +780,14 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
         if (ckpt) return cudaErrorInvalidValue;
         if (RT == 2) { SDTW_W(int8_t, 2, false) } else { SDTW_W(int8_t, 4, false) }
     }
+    if (dt == SDTW_U8) {
+        if (ckpt) return cudaErrorInvalidValue;
+        if (RT == 2) { SDTW_W(uint8_t, 2, false) } else { SDTW_W(uint8_t, 4, false) }
+    }
+    if (dt == SDTW_F16) {
+        if (ckpt) return cudaErrorInvalidValue;
+        if (RT == 2) { SDTW_W(__half, 2, false) } else { SDTW_W(__half, 4, false) }
+    }
     if (ckpt) {
         if (RT == 2) { SDTW_W(float, 2, true) } else { SDTW_W(float, 4, true) }
     }
@@ -614,16 +799,17 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 
 bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 20 || W == 24 || W == 28 || W == 32; }
 
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT)
+int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT)
 {
     // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
     // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
-    // 4-byte elements
-    (void)dt;
+    // 4-byte elements; 64-bit, so that no query length wraps to a small size
     (void)W;
-    const int npad = (N + RT - 1) / RT * RT;
-    const int esz = RT == 2 ? 16 : 32;
-    return esz * (P * kRing + npad / RT) + 4 * (npad + 2 * P);
+    if (N < 0) N = 0;
+    const int64_t npad = (N + RT - 1) / RT * RT;
+    const int64_t esz = RT == 2 ? 16 : 32;
+    const int64_t red = dt == SDTW_F16 ? 4 : 2;  // binary16 pairs reduce two (value, column) pairs per warp
+    return esz * (static_cast<int64_t>(P) * kRing + npad / RT) + 4 * (npad + red * static_cast<int64_t>(P));
 }
 
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
@@ -636,16 +822,16 @@ int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT)
     return (nsw - 1) * Pp + nt + lag_last;
 }
 
-int64_t fwd_chunks(int64_t M, int n, int W, int P, int RT)
+int64_t fwd_ckpts(int64_t M, int n, int W, int P, int RT, int KS)
 {
-    return (fwd_total_steps(M, n, W, P, RT) + kChunk - 1) / kChunk;
+    return (fwd_total_steps(M, n, W, P, RT) + KS - 1) / KS;
 }
 
-int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT)
+int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT, int KS)
 {
-    // the chunk count grows with the query length, so N bounds every query of
-    // a ragged batch
-    return fwd_chunks(M, N, W, P, RT) * 32 * P * (W + fwd_record_floats(RT));
+    // the checkpoint count grows with the query length, so N bounds every
+    // query of a ragged batch
+    return fwd_ckpts(M, N, W, P, RT, KS) * 32 * P * (W + fwd_record_floats(RT));
 }
 
 int64_t ck_slot_floats(int64_t M, int N, int K)
@@ -654,7 +840,7 @@ int64_t ck_slot_floats(int64_t M, int N, int K)
     return (windows - 1) * static_cast<int64_t>(ck_rows(N));
 }
 
-int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt)
+int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool ckpt)
 {
     int n = 0;
     dispatch(dt, W, RT, ckpt, [&](auto inst) {
@@ -674,7 +860,7 @@ cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a,
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
-    order_by_length_kernel<<<(B + 255) / 256, 256, 0, s>>>(offsets, B, order);
+    order_by_length_kernel<<<(B + kOrderThreads - 1) / kOrderThreads, kOrderThreads, 0, s>>>(offsets, B, order);
     return cudaGetLastError();
 }
 

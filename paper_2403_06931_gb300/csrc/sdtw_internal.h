@@ -24,6 +24,23 @@ static_assert((kRing & (kRing - 1)) == 0, "ring size must be a power of two");
 
 constexpr int kMaxWarpsPerQuery = 16;
 
+// Integer modes: the longest query.  Costs are compared as float bit patterns
+// (non-negative int32 patterns order like the floats they encode), so every
+// reachable cost -- at most N * 255^2 along the vertical path -- must stay
+// below 0x7f7fffff, the pattern that stands for +inf:
+// 32,896 * 65,025 = 2,139,062,400 < 2,139,095,039.
+constexpr int kIntMaxN = 32896;
+
+// FP32 mode: a strip whose left input at the first row of a tile lies more
+// than this far below the strip's integer base is rebased to that input before
+// the tile (see sdtw_forward.cu).  The backward replays the same decision.
+constexpr float kRebaseBelow = 64.f;
+
+// Dynamic shared memory one CTA may use on sm_103a.  Shared-memory sizes are
+// computed in 64-bit arithmetic and checked against this before any launch,
+// so a huge query length cannot wrap to a small size.
+constexpr int64_t kMaxSmemBytes = 227 * 1024;
+
 // Device status bits (OR-ed into the context's status word).
 constexpr int kStatusBadLength = 1;  // a ragged query longer than N
 constexpr int kStatusBadEnd = 2;     // an end index outside [0, M)
@@ -43,12 +60,12 @@ struct FwdArgs {
     int64_t* end;
     // Checkpoints for the backward pass (fr == nullptr: none).  Query q of the
     // launch uses slot q - q0 of every array below.
-    //   fr     the wavefront at the start of every chunk c of kChunk steps,
-    //          before that chunk's rebase: for thread tau, its strip's latest
-    //          row (W values relative to its base) as float4 [W/4][L], then
-    //          its record float4 [E/4][L] = {right-hand cells of its tile's
-    //          other RT-1 rows, diag, base}; chunk c at c * L * (W + E);
-    //          fr_slot floats per query (E = fwd_record_floats(RT))
+    //   fr     the wavefront at the start of step c * ck_stride for every
+    //          c >= 1, before a rebase due at that step: for thread tau, its
+    //          strip's latest row (W values relative to its base) as float4
+    //          [W/4][L], then its record float4 [E/4][L] = {right-hand cells of
+    //          its tile's other RT-1 rows, diag, base}; checkpoint c at
+    //          c * L * (W + E); fr_slot floats per query (E = fwd_record_floats(RT))
     //   colck  the left inputs of the strip whose first column is bK (b >= 1),
     //          in that strip's base: window b at (b - 1) * ck_rows(N), one per
     //          row (tiles past the query's end included);
@@ -59,6 +76,8 @@ struct FwdArgs {
     float* colck;
     int64_t ck_slot;
     int32_t K;    // window width: column checkpoint stride (8 W)
+    int32_t ck_stride;      // steps between wavefront checkpoints: 16, 32 or 64
+    int32_t rebase_period;  // steps between FP32 rebases: ckpt_rebase_period(stride) of the context's checkpointing plan, else kChunk
     float* ck_cost;
     int64_t* ck_end;
     int* status;
@@ -71,16 +90,18 @@ struct FwdPlan {
     int W = 16;          // segment width: reference columns per thread
     int P = 8;           // warps per query chain
     int RT = 2;          // query rows per thread per step (tile height)
+    int KS = kChunk;     // with checkpoints: steps between wavefront checkpoints (16, 32 or 64)
     bool persistent = false;
     int grid = 0;
     int block = 0;
-    int smem = 0;
+    int64_t smem = 0;    // dynamic shared memory per CTA (launchable only if <= kMaxSmemBytes)
 };
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
-int fwd_smem_bytes(sdtw_dtype dt, int N, int P, int W, int RT);
-int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int smem, int RT, bool ckpt);
+int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT);
+// 0 when smem exceeds kMaxSmemBytes or the plan cannot be resident
+int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool ckpt);
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s);
@@ -108,6 +129,8 @@ struct BwdArgs {
     const float* ck_cost;
     const int64_t* ck_end;
     int32_t W, P, RT;
+    int32_t KS;             // steps between the forward's wavefront checkpoints: a band's height in steps
+    int32_t rebase_period;  // the forward's steps between rebases
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
     int64_t* span;   // [B][2] first and last column of each query's path
     int* status;
@@ -115,17 +138,22 @@ struct BwdArgs {
 };
 
 // Checkpoint geometry of a forward plan (sdtw_forward.cu): floats of one
-// thread's record, chunks of the wavefront schedule for a query of n rows, and
-// the per-query slot sizes of the two checkpoint arrays.
+// thread's record, wavefront checkpoints (one every KS steps) of the schedule
+// for a query of n rows, and the per-query slot sizes of the two checkpoint
+// arrays.  Checkpoint strides are 16, 32 or 64 steps; the checkpointing fill
+// rebases every max(kChunk, KS) steps, so that no band of KS steps spans a
+// rebase.
 __host__ __device__ constexpr int fwd_record_floats(int RT) { return RT == 2 ? 4 : 8; }
 __host__ __device__ constexpr int ck_rows(int N) { return (N + 3) / 4 * 4; }
-int64_t fwd_chunks(int64_t M, int n, int W, int P, int RT);
-int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT);
+constexpr bool ckpt_stride_supported(int KS) { return KS == 16 || KS == 32 || KS == 64; }
+constexpr int ckpt_rebase_period(int KS) { return KS > kChunk ? KS : kChunk; }
+int64_t fwd_ckpts(int64_t M, int n, int W, int P, int RT, int KS);
+int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT, int KS);
 int64_t ck_slot_floats(int64_t M, int N, int K);
 
 // Backward launches (sdtw_backward.cu).
 bool bwd_width_supported(int W);
-int bwd_smem_bytes(int N, int W, int RT);
+int64_t bwd_smem_bytes(int64_t N, int W, int RT, int KS);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);

@@ -58,10 +58,11 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
                                             const int64_t* offsets, int32_t B, int32_t N, void* cost,
                                             int64_t* end, void* stream)
 {
-    if (dtype != SDTW_F32 && dtype != SDTW_I8) return SDTW_E_INVALID;
+    if (dtype != SDTW_F32 && dtype != SDTW_I8 && dtype != SDTW_U8 && dtype != SDTW_F16) return SDTW_E_INVALID;
+    if (dtype == SDTW_F16 && offsets) return SDTW_E_UNSUPPORTED;  // binary16 pairs: uniform batches only
     if (B < 0 || M < 1 || N < 1 || M > INT_MAX / 2) return SDTW_E_INVALID;
     if (B > SDTW_NOALLOC_MAX_BATCH) return SDTW_E_INVALID;  // the order array holds at most this many queries
-    if (dtype == SDTW_I8 && N > 33000) return SDTW_E_INVALID;
+    if ((dtype == SDTW_I8 || dtype == SDTW_U8) && N > sdtw::kIntMaxN) return SDTW_E_INVALID;  // costs below the +inf pattern
     if (B == 0) return SDTW_OK;
     if (!ref || !queries || !cost || !end) return SDTW_E_INVALID;
 
@@ -73,7 +74,7 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     plan.block = 32 * plan.P;
     plan.smem = sdtw::fwd_smem_bytes(dtype, N, plan.P, plan.W, plan.RT);
     plan.persistent = true;
-    if (plan.smem > 227 * 1024) return SDTW_E_UNSUPPORTED;
+    if (plan.smem > sdtw::kMaxSmemBytes) return SDTW_E_UNSUPPORTED;  // 64-bit size: no wrap for any N
     if (sdtw::fwd_total_steps(M, N, plan.W, plan.P, plan.RT) > INT_MAX - 4 * sdtw::kChunk) return SDTW_E_UNSUPPORTED;
 
     int32_t* scratch = nullptr;
@@ -102,6 +103,8 @@ extern "C" sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, i
     a.end = end;
     a.fr = nullptr;  // no checkpoints
     a.K = 1;
+    a.ck_stride = sdtw::kChunk;
+    a.rebase_period = sdtw::kChunk;
     a.status = scratch + kStatus;
     a.queue = scratch + kCounter;
     a.order = nullptr;

@@ -29,7 +29,7 @@ SEED_BASE = 240306931
 __all__ = [
     "SEED_BASE", "Workload", "rng_for", "random_walk", "znorm", "quantize_i8",
     "planted_batch", "tiny", "small_fp32", "paper_fp32", "paper_i8",
-    "ragged_fp32", "grad_subset", "by_name",
+    "ragged_fp32", "stretched", "grad_subset", "by_name",
 ]
 
 
@@ -198,6 +198,28 @@ def ragged_fp32(seed: int = SEED_BASE + 4, B: int = 2048, n_lo: int = 200,
                     flat.astype(np.float32), offsets, lengths, planted, seed, "f32", recipe)
 
 
+def stretched(seed: int = SEED_BASE + 6, B: int = 16, N: int = 400, M: int = 40_000,
+              step_lo: int = 4, step_hi: int = 24, noise: float = 0.05) -> Workload:
+    """Queries that are the reference subsampled by an integer step in
+    [step_lo, step_hi] (plus noise, z-normalised): each optimal path runs about
+    `step` columns per row, long horizontal runs across the reference."""
+    rng = rng_for(seed)
+    ref = znorm(random_walk(rng, M))
+    qs, planted = [], np.zeros(B, dtype=np.int64)
+    for q in range(B):
+        step = int(rng.integers(step_lo, step_hi + 1))
+        span = step * (N - 1) + 1
+        o = int(rng.integers(0, max(1, M - span)))
+        cut = ref[o:o + span:step][:N]
+        if cut.shape[0] < N:
+            cut = np.resize(cut, N)
+        qs.append(znorm(cut + noise * rng.standard_normal(N)))
+        planted[q] = o
+    recipe = dict(ref="znorm(cumsum N(0,1))", M=M, B=B, N=N, step=(step_lo, step_hi), noise_sigma=noise, seed=seed)
+    return Workload(f"sdtw_stretched_{B}x{N}_vs_{M}", ref.astype(np.float32), np.stack(qs).astype(np.float32),
+                    None, np.full(B, N, dtype=np.int64), planted, seed, "f32", recipe)
+
+
 def grad_subset(seed: int = SEED_BASE + 5) -> Workload:
     """Gradient-check subset: 8 queries x 64 samples vs a 512-sample reference."""
     return _uniform("sdtw_grad_8x64_vs_512", seed, 8, 64, 512, 0.1, 0.1)
@@ -205,5 +227,5 @@ def grad_subset(seed: int = SEED_BASE + 5) -> Workload:
 
 def by_name(name: str, **kw) -> Workload:
     table = {"small": small_fp32, "paper": paper_fp32, "paper_i8": paper_i8,
-             "ragged": ragged_fp32, "grad": grad_subset, "tiny": tiny}
+             "ragged": ragged_fp32, "grad": grad_subset, "tiny": tiny, "stretched": stretched}
     return table[name](**kw)

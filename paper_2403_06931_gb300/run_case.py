@@ -18,7 +18,7 @@ from .sdtw import SdtwContext
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="paper", choices=["paper", "ragged", "small", "grad"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "ragged", "small", "grad", "stretched"])
     ap.add_argument("--B", type=int, default=None, help="queries (default: the workload's)")
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--M", type=int, default=None)
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--seg-width", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--ckpt-stride", type=int, default=0, help="steps between wavefront checkpoints (16, 32, 64)")
     ap.add_argument("--keep-checkpoints", action="store_true",
                     help="the forward stores backward checkpoints (implied by --backward)")
     ap.add_argument("--znorm", action="store_true",
@@ -53,7 +54,8 @@ def main():
     ctx = SdtwContext(dtype=a.dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=N,
                       max_total_query_len=qs.numel(), grad=a.backward or a.keep_checkpoints,
                       keep_checkpoints=a.backward or a.keep_checkpoints,
-                      seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows)
+                      seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows,
+                      ckpt_stride=a.ckpt_stride)
     if a.autotune:
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None

@@ -2,8 +2,9 @@
 
 PyTorch supplies device memory and streams; every step of the computation runs
 in libsdtw.so (see capi.py).  Tensors must already be on the context's CUDA
-device, contiguous, with the element type of the context (float32, or int8
-for the integer mode); nothing is converted or copied here.
+device, contiguous, with the element type of the context (float32; int8 for
+the integer mode; uint8 codebook codes; float16 for the binary16 mode);
+nothing is converted or copied here.
 
     ctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N)
     cost, end = ctx.forward(ref, queries)              # uniform [B, N]
@@ -34,8 +35,8 @@ class SdtwContext:
                  max_batch: int = 512, max_query_len: int = 2000, max_total_query_len: int | None = None,
                  grad: bool = False, keep_checkpoints: bool = False, seg_width: int = 0,
                  warps_per_query: int = 0, ckpt_stride: int = 0, mem_cap_bytes: int = 0, tile_rows: int = 0,
-                 znorm_queries: bool = False):
-        lib_dtype = {"f32": capi.SDTW_F32, "i8": capi.SDTW_I8}[dtype]
+                 znorm_queries: bool = False, check_status: bool = True):
+        lib_dtype = {"f32": capi.SDTW_F32, "i8": capi.SDTW_I8, "u8": capi.SDTW_U8, "f16": capi.SDTW_F16}[dtype]
         cfg = capi.sdtw_config_init()
         cfg.dtype = lib_dtype
         cfg.device = torch.cuda.current_device() if device is None else int(device)
@@ -58,6 +59,9 @@ class SdtwContext:
         self.device = cfg.device
         self.cfg = cfg
         self.grad = bool(cfg.flags & capi.SDTW_FLAG_GRAD)
+        # SdtwFunction.backward reads the device status word after each backward
+        # (one stream synchronisation) and raises on a device-side error
+        self.check_status = bool(check_status)
 
     # -- helpers --------------------------------------------------------------
     def _dims(self, ref, queries, offsets, N):
@@ -82,7 +86,7 @@ class SdtwContext:
         """(cost [B], end [B] int64) of every query (sdtw_forward)."""
         self._check(ref, queries, offsets)
         B, N, M = self._dims(ref, queries, offsets, N)
-        cdt = torch.int32 if self.dtype == "i8" else torch.float32
+        cdt = torch.float32 if self.dtype in ("f32", "f16") else torch.int32
         if out is None:
             cost = torch.empty(B, dtype=cdt, device=ref.device)
             end = torch.empty(B, dtype=torch.int64, device=ref.device)
@@ -124,7 +128,7 @@ class SdtwContext:
         """Time the candidate plans on this batch and keep the fastest (sdtw_autotune)."""
         self._check(ref, queries, offsets)
         B, N, M = self._dims(ref, queries, offsets, N)
-        cdt = torch.int32 if self.dtype == "i8" else torch.float32
+        cdt = torch.float32 if self.dtype in ("f32", "f16") else torch.int32
         cost = torch.empty(B, dtype=cdt, device=ref.device)
         end = torch.empty(B, dtype=torch.int64, device=ref.device)
         st, plan = capi.sdtw_autotune(self.handle, _ptr(ref), M, _ptr(queries), _ptr(offsets), B, N,
@@ -172,8 +176,16 @@ class SdtwFunction(torch.autograd.Function):
     @staticmethod
     def backward(fctx, grad_cost, grad_end):
         ref, queries, end = fctx.saved_tensors
-        gq, gr, _ = fctx.sctx.backward(ref, queries, end, grad_cost.contiguous(), offsets=fctx.offsets,
-                                       N=fctx.N)
+        sctx = fctx.sctx
+        gq, gr, _ = sctx.backward(ref, queries, end, grad_cost.contiguous(), offsets=fctx.offsets, N=fctx.N)
+        if sctx.check_status:
+            # the status word collects what the forward and the backward found
+            # on the device (a ragged query longer than N, an end outside the
+            # reference, a recompute that missed the forward's cost): a gradient
+            # computed past any of these is not returned
+            st = sctx.device_status()
+            if st != capi.SDTW_OK:
+                raise capi.SdtwError(st, "sdtw_backward (device status)")
         return gr, gq, None, None, None
 
 
@@ -194,6 +206,28 @@ def znormalize(x, offsets=None, out=None, stream=None):
         out = torch.empty_like(x)
     st = capi.sdtw_znormalize(_ptr(x), _ptr(out), _ptr(offsets), int(B), int(N), _stream_ptr(stream))
     capi.check(st, "sdtw_znormalize")
+    return out
+
+
+def codebook_fit(ref, sigmas: float = 4.0, stream=None):
+    """The reference codebook (sdtw_codebook_fit): a float32 CUDA tensor
+    [lo, 1/step, step, 0] for 256 equal bins over mean +- sigmas * S."""
+    if not ref.is_cuda or not ref.is_contiguous() or ref.dtype != torch.float32:
+        raise ValueError("ref must be a contiguous float32 CUDA tensor")
+    params = torch.empty(4, dtype=torch.float32, device=ref.device)
+    st = capi.sdtw_codebook_fit(_ptr(ref), ref.numel(), float(sigmas), _ptr(params), _stream_ptr(stream))
+    capi.check(st, "sdtw_codebook_fit")
+    return params
+
+
+def codebook_encode(x, params, out=None, stream=None):
+    """uint8 codes of x under a codebook (sdtw_codebook_encode); same shape as x."""
+    if not x.is_cuda or not x.is_contiguous() or x.dtype != torch.float32:
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    if out is None:
+        out = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    st = capi.sdtw_codebook_encode(_ptr(x), x.numel(), _ptr(params), _ptr(out), _stream_ptr(stream))
+    capi.check(st, "sdtw_codebook_encode")
     return out
 
 

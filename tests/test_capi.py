@@ -119,3 +119,46 @@ def test_binding_fails_loudly_without_library(tmp_path):
     finally:
         capi._lib = saved
         importlib.reload  # keep the module state as it was
+
+
+# A query length whose shared-memory size, computed in 32-bit arithmetic, would
+# wrap to a small positive number (12 * 357,913,944 + 16,416 = 2^32 + 16,448 for
+# four warps of 4-row tiles).  Every entry point must reject it on the host,
+# before any device work, so these calls are safe without a GPU.
+WRAPPING_N = 357_913_944
+
+
+def test_query_lengths_beyond_shared_memory_are_rejected_on_the_host(lib):
+    cfg = capi.sdtw_config_init()
+    cfg.max_query_len = WRAPPING_N
+    cfg.max_total_query_len = WRAPPING_N
+    assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_UNSUPPORTED
+    cfg.max_query_len = 1 << 20
+    assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_UNSUPPORTED
+    fake = 256  # never dereferenced: the calls return before touching the device
+    for dtype in (capi.SDTW_F32, capi.SDTW_I8):
+        for offsets in (None, fake):
+            for n in (WRAPPING_N, 2_000_000_000, 40_000):
+                if dtype == capi.SDTW_I8 and n > 32_896:
+                    want = capi.SDTW_E_INVALID          # the int32 cost bound comes first
+                else:
+                    want = capi.SDTW_E_UNSUPPORTED
+                st = capi.sdtw_forward_noalloc(dtype, fake, 1000, fake, offsets, 3, n, fake, fake, None)
+                assert st == want, (dtype, offsets, n, st)
+
+
+def test_reserved_spin_limit_must_be_zero(lib):
+    cfg = capi.sdtw_config_init()
+    cfg.spin_limit = 1000
+    assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_INVALID
+
+
+def test_checkpoint_strides_accepted_by_create(lib):
+    # 16, 32 and 64 steps are the strides the library has; any other positive
+    # stride is rejected before any device work (a negative one is invalid)
+    for ks, want in ((48, capi.SDTW_E_UNSUPPORTED), (8, capi.SDTW_E_UNSUPPORTED), (128, capi.SDTW_E_UNSUPPORTED),
+                     (-16, capi.SDTW_E_INVALID)):
+        cfg = capi.sdtw_config_init()
+        cfg.ckpt_stride = ks
+        cfg.flags = capi.SDTW_FLAG_GRAD
+        assert capi.sdtw_create(cfg)[0] == want, ks

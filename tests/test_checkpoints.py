@@ -1,18 +1,19 @@
 """CPU model of the backward checkpoints and of the backward's band replay.
 
-The checkpointing forward (csrc/sdtw_forward.cu) stores, at the end of every
-chunk of kChunk steps, the state of its wavefront: each thread's latest row
-(its strip of W columns, relative to the thread's integer base), the right-hand
+The checkpointing forward (csrc/sdtw_forward.cu) stores, every KS steps
+(KS = 16, 32 or 64), the state of its wavefront: each thread's latest row (its
+strip of W columns, relative to the thread's integer base), the right-hand
 cells of its tile's other rows, its diagonal input and its base, as they stand
-before the next chunk's rebase (the backward redoes that rebase).  The rows a
-wavefront holds form an anti-diagonal staircase (thread l is one tile behind
-thread l-1), so these are checkpoints along anti-diagonals, one every kChunk
-steps.  Beside them, the strip that starts at every K-th column stores the left
+before a rebase due at that step (the backward redoes that rebase; the fill
+rebases every max(kChunk, KS) steps, so a 16-step checkpoint between rebases
+is already in its base).  The rows a wavefront holds form an anti-diagonal
+staircase (thread l is one tile behind thread l-1), so these are checkpoints
+along anti-diagonals, one every KS steps.  Beside them, the strip that starts at every K-th column stores the left
 inputs it used (its boundary column, already converted into its own base).
 
 The backward (csrc/sdtw_backward.cu) recomputes one band at a time: the cells
-that the strips of one K-column window computed during one chunk, a
-parallelogram.  Starting from the chunk's stored wavefront and the window's
+that the strips of one K-column window computed during the KS steps after one
+checkpoint, a parallelogram.  Starting from the chunk's stored wavefront and the window's
 stored boundary column, with the forward's own operations, it reproduces the
 forward's FP32 values bit for bit.
 
@@ -33,6 +34,8 @@ import numpy as np
 import pytest
 
 K_CHUNK = 32   # csrc/sdtw_internal.h kChunk
+REBASE_BELOW = 64.0   # csrc/sdtw_internal.h kRebaseBelow
+STRIDES = (16, 32, 64)   # checkpoint strides the library supports
 INF = float("inf")
 
 
@@ -78,16 +81,30 @@ def rebase(B, first):
     return bn, r32(bn - B)
 
 
-def frontier_state(fw, c, tau):
-    """A thread's state at the start of chunk c, after the rebase."""
+def rebase_to_left(B, left0):
+    """The forward's rebase to a left input far below the strip's base: (new
+    base, shift), or None when the tile's first-row left input is not that low."""
+    if not left0 < -REBASE_BELOW:
+        return None
+    bn = float(math.floor(r32(B + left0)))
+    return bn, r32(bn - B)
+
+
+def frontier_state(fw, pl, c, tau):
+    """A thread's state at checkpoint c (step c * KS), after the rebase when
+    one is due at that step."""
     prev, alast, diag, B = fw["frontier"][(c, tau)]
+    if (c * pl.KS) % pl.R:
+        return prev[:], alast[:], diag, B
     bn, dl = rebase(B, prev[0])
     return [r32(v - dl) for v in prev], [r32(v - dl) for v in alast], r32(diag - dl), bn
 
 
 class Plan:
-    def __init__(self, n, M, P, W, RT, K):
+    def __init__(self, n, M, P, W, RT, K, KS=K_CHUNK):
         self.n, self.M, self.P, self.W, self.RT, self.K = n, M, P, W, RT, K
+        self.KS = KS                      # steps between wavefront checkpoints
+        self.R = max(K_CHUNK, KS)         # steps between rebases
         self.L = 32 * P
         self.S = self.L * W
         self.nsw = -(-M // self.S)
@@ -96,13 +113,13 @@ class Plan:
         self.nt = -(-n // RT)
         self.Pp = max(self.nt, self.lag_last + K_CHUNK)
         self.total = (self.nsw - 1) * self.Pp + self.nt + self.lag_last
-        self.chunks = -(-self.total // K_CHUNK)
+        self.ckpts = -(-self.total // KS)
 
     def band_of(self, i, j):
-        """(chunk, window) of the band holding cell (i, j)."""
+        """(checkpoint, window) of the band holding cell (i, j)."""
         s, tau = j // self.S, (j % self.S) // self.W
         t = i // self.RT + self.lag[tau] + s * self.Pp
-        return t // K_CHUNK, j // self.K
+        return t // self.KS, j // self.K
 
 
 def model_forward(x, y, pl):
@@ -122,14 +139,16 @@ def model_forward(x, y, pl):
     ring, colbuf = {}, {}
     frontier, colck, D = {}, {}, {}
     best, best_col = INF, None
+    triggers = 0
     for t in range(pl.total):
-        if t % K_CHUNK == 0:
-            # the wavefront as the previous chunk left it (before the rebase)
-            c = t // K_CHUNK
+        if t % pl.KS == 0:
+            # the wavefront as the previous steps left it (before a rebase due now)
+            c = t // pl.KS
             for tau in range(L):
                 pp, ss = p[tau], s[tau]
                 if (1 <= pp <= pl.nt and ss < pl.nsw) or (pp == 0 and ss >= 1 and pl.Pp == pl.nt):
                     frontier[(c, tau)] = (prev[tau][:], alast[tau][:], diag[tau], B[tau])
+        if t % pl.R == 0:
             for tau in range(L):
                 bn, dl = rebase(B[tau], prev[tau][0])
                 prev[tau] = [r32(v - dl) for v in prev[tau]]
@@ -161,6 +180,18 @@ def model_forward(x, y, pl):
                 B[tau] = 0.0
             dd = r32(rb[tau] - B[tau])
             left = [r32(v + dd) for v in recv[tau]]
+            b0 = base[tau]
+            if b0 % K == 0 and 0 < b0 < M:
+                for rr in range(RT):                 # stored as converted, before any shift
+                    if RT * pt + rr < n:
+                        colck[(b0 // K, RT * pt + rr)] = left[rr]
+            shift = rebase_to_left(B[tau], left[0])
+            if shift:
+                triggers += 1
+                B[tau], dl = shift
+                prev[tau] = [r32(v - dl) for v in prev[tau]]
+                diag[tau] = r32(diag[tau] - dl)
+                left = [r32(v - dl) for v in left]
             rows, codes, above, dg0 = [], [], prev[tau], diag[tau]
             for rr in range(RT):
                 xv = xs[RT * pt + rr]
@@ -178,7 +209,6 @@ def model_forward(x, y, pl):
             alast[tau] = [rows[rr][W - 1] for rr in range(RT - 1)]
             prev[tau] = rows[RT - 1]
             diag[tau] = left[RT - 1]
-            b0 = base[tau]
             for rr in range(RT):
                 i = RT * pt + rr
                 if i >= n:
@@ -186,8 +216,6 @@ def model_forward(x, y, pl):
                 for j in range(W):
                     if b0 + j < M:
                         D[(i, b0 + j)] = (rows[rr][j], B[tau], codes[rr][j])
-                if b0 % K == 0 and 0 < b0 < M:
-                    colck[(b0 // K, i)] = left[rr]
                 if i == n - 1:
                     for j in range(W):
                         if b0 + j < M:
@@ -205,7 +233,8 @@ def model_forward(x, y, pl):
             if p[tau] == pl.Pp:
                 p[tau] = 0
                 s[tau] += 1
-    return {"D": D, "frontier": frontier, "colck": colck, "cost": best, "end": best_col, "x": xs, "y": ys}
+    return {"D": D, "frontier": frontier, "colck": colck, "cost": best, "end": best_col, "x": xs, "y": ys,
+            "triggers": triggers}
 
 
 def model_replay(fw, pl, c, b):
@@ -219,15 +248,15 @@ def model_replay(fw, pl, c, b):
     info = []
     for d in range(nstrip):
         tau = tau0 + d
-        ps = c * K_CHUNK - pl.lag[tau] - s * pl.Pp
-        r0, r1 = RT * max(0, ps), min(n, RT * min(pl.nt, ps + K_CHUNK))
+        ps = c * pl.KS - pl.lag[tau] - s * pl.Pp
+        r0, r1 = RT * max(0, ps), min(n, RT * min(pl.nt, ps + pl.KS))
         if ps > pl.nt:
-            info.append((ps, r0, r1, 0.0, None))   # finished before this chunk
+            info.append((ps, r0, r1, 0.0, None))   # finished before this band
             continue
         if ps >= 1:
             # the strip's state after tile ps-1; with ps == nt its band is empty
             # but its last tile's right-hand cells feed the next strip
-            pr, al, dg, Bd = frontier_state(fw, c, tau)
+            pr, al, dg, Bd = frontier_state(fw, pl, c, tau)
             edge = al + [pr[W - 1]]          # rows RT*(ps-1) .. RT*ps-1, last column
         else:
             pr, dg, Bd, edge = [0.0] * W, 0.0, 0.0, None
@@ -235,17 +264,30 @@ def model_replay(fw, pl, c, b):
         cols = [c0 + d * W + k for k in range(W)]
         yv = [fw["y"][j] if j < M else 0.0 for j in cols]
         above = pr
+        Btile, dltile = Bd, 0.0
         for r in range(r0, r1):
+            tile_start = r % RT == 0
+            if tile_start:
+                Btile = Bd                   # the tile's left inputs are converted into this base
             if d == 0:
                 lf = INF if b == 0 else fw["colck"][(b, r)]
             else:
                 ps_l, r0_l, _, B_l, edge_l = info[d - 1]
-                dd = r32(B_l - Bd)
                 if r >= r0_l:
-                    v = out[(r, c0 + d * W - 1)][0]
+                    v, B_src, _ = out[(r, c0 + d * W - 1)]
                 else:
-                    v = edge_l[r - RT * (ps_l - 1)]
-                lf = r32(v + dd)
+                    v, B_src = edge_l[r - RT * (ps_l - 1)], B_l
+                lf = r32(v + r32(B_src - Btile))
+            if tile_start:
+                # the forward's rebase to a far lower left input, decided on the tile's first row
+                dltile = 0.0
+                shift = rebase_to_left(Bd, lf)
+                if shift:
+                    Bd, dltile = shift
+                    above = [r32(u - dltile) for u in above]
+                    dg = r32(dg - dltile)
+            if dltile != 0.0:
+                lf = r32(lf - dltile)
             cur = []
             for k in range(W):
                 up = above[k]
@@ -270,7 +312,7 @@ CASES = [
 ]
 
 
-def _setup(P, W, RT, n, M, seed):
+def _setup(P, W, RT, n, M, seed, KS=K_CHUNK):
     rng = np.random.default_rng(seed)
     y = np.cumsum(rng.standard_normal(M))
     y = (y - y.mean()) / y.std()
@@ -278,17 +320,18 @@ def _setup(P, W, RT, n, M, seed):
     x = y[o:o + n] if o + n <= M else rng.standard_normal(n)
     x = x + 0.1 * rng.standard_normal(n)
     x = (x - x.mean()) / (x.std() or 1.0)
-    pl = Plan(n, M, P, W, RT, 8 * W)
+    pl = Plan(n, M, P, W, RT, 8 * W, KS)
     return pl, model_forward(x, y, pl)
 
 
+@pytest.mark.parametrize("KS", STRIDES)
 @pytest.mark.parametrize("P,W,RT,n,M", CASES)
-def test_band_replay_is_bit_exact(P, W, RT, n, M):
-    pl, fw = _setup(P, W, RT, n, M, seed=n * 7 + M)
+def test_band_replay_is_bit_exact(P, W, RT, n, M, KS):
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 7 + M, KS=KS)
     D = fw["D"]
     assert len(D) == n * M
     covered = {}
-    for c in range(pl.chunks):
+    for c in range(pl.ckpts):
         for b in range(-(-M // pl.K)):
             for key, val in model_replay(fw, pl, c, b).items():
                 if key[1] >= M:
@@ -317,9 +360,10 @@ def _walk(code_of, n, end):
     return path
 
 
+@pytest.mark.parametrize("KS", STRIDES)
 @pytest.mark.parametrize("P,W,RT,n,M", CASES[:3])
-def test_walk_through_bands_matches_full_matrix(P, W, RT, n, M):
-    pl, fw = _setup(P, W, RT, n, M, seed=n * 11 + M)
+def test_walk_through_bands_matches_full_matrix(P, W, RT, n, M, KS):
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 11 + M, KS=KS)
     full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
     cache = {}
 
@@ -348,7 +392,7 @@ def flat_checkpoints(fw, pl):
     """The forward's checkpoint arrays in their device layouts (one query)."""
     W, RT, L = pl.W, pl.RT, pl.L
     E = 4 if RT == 2 else 8
-    fr = np.full(pl.chunks * L * (W + E), np.nan)
+    fr = np.full(pl.ckpts * L * (W + E), np.nan)
     for (c, tau), (prev, alast, diag, B) in fw["frontier"].items():
         base = c * L * (W + E)
         for k in range(W // 4):                       # float4 [W/4][L]: prev
@@ -375,11 +419,11 @@ def kernel_backward(fw, pl, end, RS=None):
     the path, recomputed D at the end cell, number of bands)."""
     RS = rows_per_step(pl.RT) if RS is None else RS
     n, M, W, RT, L, S, Pp, nt = pl.n, pl.M, pl.W, pl.RT, pl.L, pl.S, pl.Pp, pl.nt
-    WB, KW, KC = W // 4, 32 * (W // 4), K_CHUNK
+    WB, KW, KC = W // 4, 32 * (W // 4), pl.KS     # KC: a band's height in steps
     E = 4 if RT == 2 else 8
     fr, ck = flat_checkpoints(fw, pl)
     xs, ys_all = fw["x"], fw["y"]
-    lag = lambda tau: (tau >> 5) * (32 + KC) + (tau & 31)  # noqa: E731
+    lag = lambda tau: (tau >> 5) * (32 + K_CHUNK) + (tau & 31)  # noqa: E731
     wi, wj = n - 1, end
     cells, first, v_end, bands = [], True, None, 0
     done = False
@@ -400,6 +444,8 @@ def kernel_backward(fw, pl, end, RS=None):
         ys = [ys_all[c0 + k] if c0 + k < M else 0.0 for k in range(KW)]
         lcol = [ck[(b - 1) * (-(-n // 4) * 4) + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
         frc = c * L * (W + E)
+        redo = (c * KC) % pl.R == 0       # a rebase was due at the band's first step
+        rb = (lambda B0, f: rebase(B0, f)) if redo else (lambda B0, f: (B0, 0.0))  # noqa: E731
         fr_at = lambda j, th: fr[frc + ((j >> 2) * L + th) * 4 + (j & 3)]             # noqa: E731
         rec_at = lambda e, th: fr[frc + (((W >> 2) + (e >> 2)) * L + th) * 4 + (e & 3)]  # noqa: E731
         lanes = []
@@ -410,22 +456,22 @@ def kernel_backward(fw, pl, end, RS=None):
                       rf_left=RT * max(0, ps + 1), e=[0.0] * 4, dd=0.0)
             tau = tau0 + d
             if 1 <= ps <= nt:
-                Bn, dl = rebase(rec_at(2 if RT == 2 else 4, tau), fr_at(0, tau))
+                Bn, dl = rb(rec_at(2 if RT == 2 else 4, tau), fr_at(0, tau))
                 st["D"] = [r32(fr_at(sub * WB + k, tau) - dl) for k in range(WB)]
                 st["B"] = Bn
                 st["dg"] = r32((rec_at(RT - 1, tau) if sub == 0 else fr_at(sub * WB - 1, tau)) - dl)
             else:
                 st["D"], st["B"], st["dg"] = [0.0] * WB, 0.0, 0.0
+            st["bsrc"] = 0.0
             if sub == 0 and d >= 1:
-                bsrc = 0.0
                 if 1 <= ps + 1 <= nt:
-                    bsrc, dl = rebase(rec_at(2 if RT == 2 else 4, tau - 1), fr_at(0, tau - 1))
+                    st["bsrc"], dl = rb(rec_at(2 if RT == 2 else 4, tau - 1), fr_at(0, tau - 1))
                     if RT == 2:
                         e = [rec_at(0, tau - 1), fr_at(W - 1, tau - 1), 0.0, 0.0]
                     else:
                         e = [rec_at(0, tau - 1), rec_at(1, tau - 1), rec_at(2, tau - 1), fr_at(W - 1, tau - 1)]
                     st["e"] = [r32(v - dl) for v in e]
-                st["dd"] = r32(bsrc - st["B"])
+            st["btile"], st["dltile"] = st["B"], 0.0
             st["y"] = ys[lane * WB:(lane + 1) * WB]
             lanes.append(st)
         # lane l handles rows r .. r+RS-1 (r - rtop a multiple of RS, inside one
@@ -443,12 +489,24 @@ def kernel_backward(fw, pl, end, RS=None):
                   for lane, st in enumerate(lanes))
         for sg in range(sg0, steps):
             recv = [lanes[max(0, lane - 1)]["last"][:] for lane in range(32)]
+            brecv = [lanes[max(0, lane - 1)]["B"] for lane in range(32)]
             for lane, st in enumerate(lanes):
                 r = rtop + RS * (sg - lane)
                 hi = min(st["re"], wi + 1)
                 if not (st["rf"] <= r < hi):
                     continue
                 v = min(RS, hi - r)            # valid rows of this step
+                tile_start = r % RT == 0
+                if st["sub"] != 0 and brecv[lane] != st["B"]:
+                    # the strip's first lane rebased at these rows: follow it
+                    dl = r32(brecv[lane] - st["B"])
+                    st["D"] = [r32(u - dl) for u in st["D"]]
+                    st["dg"] = r32(st["dg"] - dl)
+                    st["B"] = brecv[lane]
+                if tile_start:
+                    st["btile"] = st["B"]
+                from_rec = r < st["rf_left"]
+                dconv = r32((st["bsrc"] if from_rec else brecv[lane]) - st["btile"])
                 lefts = []
                 for h in range(RS):
                     rr = r + h
@@ -457,8 +515,18 @@ def kernel_backward(fw, pl, end, RS=None):
                     elif st["d"] == 0:
                         lefts.append(INF if (b == 0 or h >= v) else lcol[rr - rf0])
                     else:
-                        src = recv[lane][h] if r >= st["rf_left"] else st["e"][rr - RT * st["ps"]]
-                        lefts.append(r32(src + st["dd"]))
+                        src = recv[lane][h] if not from_rec else st["e"][rr - RT * st["ps"]]
+                        lefts.append(r32(src + dconv))
+                if st["sub"] == 0:
+                    if tile_start:
+                        st["dltile"] = 0.0
+                        shift = rebase_to_left(st["B"], lefts[0])
+                        if shift:
+                            st["B"], st["dltile"] = shift
+                            st["D"] = [r32(u - st["dltile"]) for u in st["D"]]
+                            st["dg"] = r32(st["dg"] - st["dltile"])
+                    if st["dltile"] != 0.0:
+                        lefts = [r32(u - st["dltile"]) for u in lefts]
                 xv = [xs[r + h] if h < v else 0.0 for h in range(RS)]
                 ls = lefts[:]
                 dgs = [st["dg"]] + lefts[:-1]  # row h's diagonal at the strip's first column
@@ -531,13 +599,15 @@ KERNEL_CASES = [
 ]
 
 
+@pytest.mark.parametrize("KS", STRIDES)
 @pytest.mark.parametrize("two_rows", [False, True])
 @pytest.mark.parametrize("P,W,RT,n,M", KERNEL_CASES)
-def test_kernel_band_schedule_and_walk(P, W, RT, n, M, two_rows):
-    """Both step heights a band of 4-row tiles can take (2 rows or the tile)."""
+def test_kernel_band_schedule_and_walk(P, W, RT, n, M, two_rows, KS):
+    """Both step heights a band of 4-row tiles can take (2 rows or the tile),
+    every checkpoint stride."""
     if two_rows and RT == 2:
         pytest.skip("2-row tiles take 2-row steps")
-    pl, fw = _setup(P, W, RT, n, M, seed=n * 13 + M)
+    pl, fw = _setup(P, W, RT, n, M, seed=n * 13 + M, KS=KS)
     cells, v_end, bands = kernel_backward(fw, pl, fw["end"], RS=2 if two_rows else RT)
     assert v_end == fw["cost"]
     full = _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"])
@@ -550,11 +620,46 @@ def test_kernel_schedule_random_shapes():
     schedule: the banded walk equals the walk over the whole FP32 matrix and
     the end cell is recomputed bit for bit."""
     rng = np.random.default_rng(4242)
-    for _ in range(20):
+    for _ in range(24):
         P, W, RT = int(rng.choice([1, 2])), int(rng.choice([4, 8])), int(rng.choice([2, 4]))
         RS = int(rng.choice([1, 2, RT]))
+        KS = int(rng.choice(STRIDES))
         n, M = int(rng.integers(1, 240)), int(rng.integers(2, 1300))
-        pl, fw = _setup(P, W, RT, n, M, seed=int(rng.integers(0, 10**6)))
+        pl, fw = _setup(P, W, RT, n, M, seed=int(rng.integers(0, 10**6)), KS=KS)
         cells, v_end, _ = kernel_backward(fw, pl, fw["end"], RS=RS)
-        assert v_end == fw["cost"], (P, W, RT, RS, n, M)
-        assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"]), (P, W, RT, RS, n, M)
+        assert v_end == fw["cost"], (P, W, RT, RS, KS, n, M)
+        assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"]), (P, W, RT, RS, KS, n, M)
+
+
+def _stretched(seed, M=1400, step=8, n=150):
+    """A query that is the reference subsampled by `step` (plus a little noise):
+    its optimal path runs horizontally for about `step` columns per row, so
+    cheap values cross strips whose own cells are far more expensive -- the
+    case the forward's rebase to a low left input exists for."""
+    rng = np.random.default_rng(seed)
+    y = np.cumsum(rng.standard_normal(M))
+    y = (y - y.mean()) / y.std()
+    x = y[100:100 + step * n:step] + 0.05 * rng.standard_normal(n)
+    return (x - x.mean()) / x.std(), y
+
+
+@pytest.mark.parametrize("KS", STRIDES)
+@pytest.mark.parametrize("P,W,RT", [(1, 4, 2), (2, 4, 4), (1, 8, 4)])
+def test_rebase_to_low_left_inputs_is_replayed(P, W, RT, KS):
+    """With many rebases to low left inputs: every band replays bit for bit,
+    and the lane schedule's walk equals the walk over the whole FP32 matrix."""
+    for k in range(6):   # the first seeded input on which the forward rebases to a left input
+        x, y = _stretched(seed=10 * W + RT + KS + 1000 * k)
+        pl = Plan(len(x), len(y), P, W, RT, 8 * W, KS)
+        fw = model_forward(x, y, pl)
+        if fw["triggers"] > 0:
+            break
+    assert fw["triggers"] > 0
+    for c in range(pl.ckpts):
+        for b in range(-(-pl.M // pl.K)):
+            for key, val in model_replay(fw, pl, c, b).items():
+                if key[1] < pl.M:
+                    assert val == fw["D"][key], (c, b, key)
+    cells, v_end, _ = kernel_backward(fw, pl, fw["end"])
+    assert v_end == fw["cost"]
+    assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], pl.n, fw["end"])

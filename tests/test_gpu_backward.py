@@ -143,12 +143,35 @@ def test_backward_shapes(gpu, B, N, M, W, RT, P):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
 
 
+@pytest.mark.parametrize("P", [2, 5])
 @pytest.mark.parametrize("RT", [2, 4])
 @pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
-def test_backward_every_tile_height_and_width(gpu, RT, W):
+def test_backward_every_tile_height_and_width(gpu, RT, W, P):
     # checkpoints taken by every checkpointing forward variant
     w = inputs.tiny(B=3, N=700, M=9000, seed=400 + RT + W)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=2)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=P)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+
+
+@pytest.mark.parametrize("KS", [16, 32, 64])
+@pytest.mark.parametrize("RT", [2, 4])
+def test_backward_every_checkpoint_stride(gpu, RT, KS):
+    # bands of 16, 32 or 64 forward steps, with several warps and sweeps
+    w = inputs.tiny(B=4, N=600, M=12000, seed=430 + RT + KS)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=24, tile_rows=RT, warps_per_query=3, ckpt_stride=KS)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    gy_sum = check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+    assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
+
+
+@pytest.mark.parametrize("KS", [16, 32, 64])
+def test_backward_stretched_paths(gpu, KS):
+    # long horizontal runs: the forward rebases strips to low left inputs, and
+    # the backward must replay every such rebase to reproduce the forward's
+    # values (the device checks the end cell bit for bit)
+    w = inputs.stretched(B=8, N=300, M=30000)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=KS)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
@@ -170,27 +193,29 @@ def test_backward_ragged(gpu):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
 
 
-def _ckpt_floats_per_query(M, N, W, P, RT):
+def _ckpt_floats_per_query(M, N, W, P, RT, KS):
     """Backward workspace per query (floats) of a checkpointing plan: the
-    wavefront slot (one record of W + 4 or W + 8 floats per thread and chunk of
-    32 steps), the boundary columns every 8 W columns (rows padded to 4), a gradient row and 7
-    scalars (the layout the library documents)."""
+    wavefront slot (one record of W + 4 or W + 8 floats per thread and
+    checkpoint, one checkpoint every KS steps), the boundary columns every 8 W
+    columns (rows padded to 4), a gradient row and 7 scalars (the layout the
+    library documents)."""
     S, lag_last = 32 * P * W, (P - 1) * 64 + 31
     nsw, nt = -(-M // S), -(-N // RT)
     total = (nsw - 1) * max(nt, lag_last + 32) + nt + lag_last
-    fr = -(-total // 32) * 32 * P * (W + (4 if RT == 2 else 8))
+    fr = -(-total // KS) * 32 * P * (W + (4 if RT == 2 else 8))
     ck = (-(-M // (8 * W)) - 1) * (-(-N // 4) * 4)
     return fr + ck + M + 7
 
 
-def test_chunked_and_recomputed_backward_are_identical(gpu):
+@pytest.mark.parametrize("KS", [16, 32, 64])
+def test_chunked_and_recomputed_backward_are_identical(gpu, KS):
     w = inputs.tiny(B=9, N=200, M=4000, seed=81)
-    st = dict(seg_width=16, tile_rows=4, warps_per_query=2)
+    st = dict(seg_width=16, tile_rows=4, warps_per_query=2, ckpt_stride=KS)
     a = run_bwd(gpu, w, keep=True, **st)                          # checkpoints from the forward
     b = run_bwd(gpu, w, keep=False, **st)                         # backward re-runs the forward
     # a cap that holds the checkpoints of 4 queries: chunks of 4, 4 and 1
     fixed = 8 + 4 * w.B + 12 * w.B
-    per_q = _ckpt_floats_per_query(w.M, w.N, 16, 2, 4)
+    per_q = _ckpt_floats_per_query(w.M, w.N, 16, 2, 4, KS)
     c = run_bwd(gpu, w, keep=False, mem_cap_bytes=fixed + 4 * (4 * per_q + 32) + 8, **st)
     for u, v in ((a, b), (a, c)):
         for k in range(5):
@@ -286,6 +311,26 @@ def test_autograd_function(gpu):
     (cost * wts).sum().backward()
     gq, gr, _ = ctx.backward(ref.detach(), qs.detach(), end, wts)
     assert torch.equal(qs.grad, gq) and torch.equal(ref.grad, gr)
+    ctx.close()
+
+
+def test_autograd_raises_on_a_device_side_error(gpu):
+    # a ragged query longer than N is flagged on the device by the forward; the
+    # autograd backward reads the status word and raises instead of returning
+    # a gradient computed past the error
+    lengths = np.array([30, 80, 30], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    rng = np.random.default_rng(96)
+    ref = torch.from_numpy(rng.standard_normal(600).astype(np.float32)).to(gpu).requires_grad_(True)
+    flat = torch.from_numpy(rng.standard_normal(int(offs[-1])).astype(np.float32)).to(gpu).requires_grad_(True)
+    o = torch.from_numpy(offs).to(gpu)
+    ctx = SdtwContext(max_ref_len=600, max_batch=3, max_query_len=80, max_total_query_len=int(offs[-1]),
+                      grad=True, keep_checkpoints=True)
+    cost, end = sdtw_cost(ref, flat, ctx, offsets=o, N=40)
+    assert end[1].item() == -1 and cost[1].item() == float("inf")
+    with pytest.raises(capi.SdtwError):
+        cost[[0, 2]].sum().backward()
+    assert ctx.device_status() == capi.SDTW_OK     # read and cleared by the backward
     ctx.close()
 
 

@@ -1,0 +1,98 @@
+"""GPU binary16 mode (the paper's precision, Section 5.2) against the CPU oracle.
+
+The oracle evaluates Eq. 1 with every operation rounded to binary16 (the
+subtraction, then one fused multiply-add); the GPU packs two queries per
+thread as __half2 and must return the same binary16 cost (widened exactly to
+float) and the same end column, bit for bit.  Against the FP64 DP of the same
+binary16 samples the difference is what binary16 arithmetic makes of a long
+sum; a loose bound is checked and the error reported by bench.py.
+"""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_06931_gb300 import capi, inputs
+from paper_2403_06931_gb300.sdtw import SdtwContext
+
+pytestmark = pytest.mark.gpu
+
+
+def run_f16(dev, ref, queries, **kw):
+    r = torch.from_numpy(np.ascontiguousarray(ref, dtype=np.float16)).to(dev)
+    q = torch.from_numpy(np.ascontiguousarray(queries, dtype=np.float16)).to(dev)
+    B, N = queries.shape
+    ctx = SdtwContext(dtype="f16", max_ref_len=len(ref), max_batch=B, max_query_len=N, **kw)
+    cost, end = ctx.forward(r, q)
+    assert ctx.device_status() == capi.SDTW_OK
+    ctx.close()
+    assert cost.dtype == torch.float32
+    return cost.cpu().numpy(), end.cpu().numpy()
+
+
+def check_f16(ref, queries, idx, cost, end):
+    y = np.asarray(ref, dtype=np.float16)
+    with ThreadPoolExecutor(max_workers=oracle.default_threads()) as ex:
+        res = list(ex.map(lambda q: oracle.forward_f16(np.asarray(queries[q], np.float16), y), idx))
+    return [(q, float(cost[q]), r[0], int(end[q]), r[1]) for q, r in zip(idx, res)
+            if not (float(cost[q]) == r[0] and int(end[q]) == r[1])]
+
+
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
+@pytest.mark.parametrize("P", [1, 3, 4, 16])
+def test_every_plan_bit_exact(gpu, W, P, RT):
+    w = inputs.tiny(B=5, N=91, M=6000, seed=90)          # odd: the last pair repeats its query
+    cost, end = run_f16(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
+    assert check_f16(w.ref, w.queries, range(w.B), cost, end) == []
+
+
+@pytest.mark.parametrize("B,N,M", [(1, 1, 500), (2, 40, 1), (3, 300, 129), (4, 1000, 999), (6, 1501, 20000),
+                                   (2, 64, 4097)])
+def test_shapes_bit_exact(gpu, B, N, M):
+    w = inputs.tiny(B=B, N=N, M=M, seed=91 + B + N + M)
+    cost, end = run_f16(gpu, w.ref, w.queries)
+    assert check_f16(w.ref, w.queries, range(B), cost, end) == []
+
+
+def test_overflow_and_exact_cut(gpu):
+    # a query far from every reference sample overflows binary16 (cost +inf,
+    # end 0: every column attains it); an exact cut costs 0 at its end
+    y = np.linspace(-2, 2, 3000).astype(np.float16)
+    qs = np.stack([np.full(40, 300.0, dtype=np.float16), y[1000:1040]])
+    cost, end = run_f16(gpu, y, qs)
+    assert np.isinf(cost[0]) and end[0] == 0
+    assert cost[1] == 0.0
+    assert check_f16(y, qs, [0, 1], cost, end) == []
+
+
+def test_ragged_batches_are_unsupported(gpu):
+    ctx = SdtwContext(dtype="f16", max_ref_len=100, max_batch=2, max_query_len=10, max_total_query_len=20)
+    z = torch.zeros(100, dtype=torch.float16, device=gpu)
+    o = torch.tensor([0, 5, 10], dtype=torch.int64, device=gpu)
+    c = torch.empty(2, device=gpu)
+    e = torch.empty(2, dtype=torch.int64, device=gpu)
+    s = torch.cuda.current_stream().cuda_stream
+    assert capi.sdtw_forward(ctx.handle, z.data_ptr(), 100, z.data_ptr(), o.data_ptr(), 2, 10, c.data_ptr(),
+                             e.data_ptr(), s) == capi.SDTW_E_UNSUPPORTED
+    ctx.close()
+
+
+def test_paper_batch_full_size_sampled(gpu):
+    """512 x 2,000 vs 100,000 in binary16: 24 sampled queries (and their pair
+    partners) bit-exact against the binary16 oracle; the difference from the
+    FP64 DP of the same samples stays within a percent of the cost."""
+    w = inputs.paper_fp32()
+    q16 = w.queries.astype(np.float16)
+    y16 = w.ref.astype(np.float16)
+    cost, end = run_f16(gpu, y16, q16)
+    assert np.isfinite(cost).all() and ((end >= 0) & (end < w.M)).all()
+    rng = np.random.default_rng(31)
+    pairs = sorted(set((2 * rng.choice(w.B // 2, size=12, replace=False)).tolist()))
+    idx = sorted(set(pairs + [p + 1 for p in pairs]))
+    assert check_f16(y16, q16, idx, cost, end) == []
+    c64, _ = oracle.forward_batch(y16.astype(np.float64), q16.astype(np.float64), indices=idx[:8])
+    rel = np.abs(cost[idx[:8]] - c64) / c64
+    assert rel.max() < 1e-2

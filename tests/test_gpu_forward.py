@@ -54,7 +54,7 @@ def test_shapes_fp32(gpu, B, N, M):
 
 @pytest.mark.parametrize("RT", [2, 4])
 @pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
-@pytest.mark.parametrize("P", [1, 2, 3, 4, 8, 16])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 8, 16])
 def test_every_plan_fp32(gpu, W, P, RT):
     w = inputs.tiny(B=3, N=91, M=6000, seed=77)
     cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
@@ -63,7 +63,7 @@ def test_every_plan_fp32(gpu, W, P, RT):
 
 @pytest.mark.parametrize("RT", [2, 4])
 @pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
-@pytest.mark.parametrize("P", [1, 4, 16])
+@pytest.mark.parametrize("P", [1, 4, 5, 16])
 def test_every_plan_i8_bit_exact(gpu, W, P, RT):
     w = inputs.paper_i8(B=4, N=70, M=5000, seed=78)
     cost, end = run_fwd(gpu, w.ref, w.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT)
@@ -83,6 +83,17 @@ def test_fast_path_plans(gpu, W, P, RT):
         wi = inputs.paper_i8(B=2, N=N, M=20000, seed=80 + N)
         cost, end = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT)
         assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
+
+
+@pytest.mark.parametrize("W", [16, 24, 32])
+def test_stretched_paths_fp32(gpu, W):
+    # queries subsampled from the reference: their paths run long horizontal
+    # stretches into strips whose own cells cost far more (the FP32 fill
+    # rebases a strip to such a low left input; without it these costs drift
+    # past the tolerance)
+    w = inputs.stretched()
+    cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W)
+    assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
 
 def test_exact_cut_has_zero_cost(gpu):
@@ -150,7 +161,8 @@ def test_ragged_query_longer_than_N_is_flagged(gpu):
     ctx.forward(ref, flat, offsets=o, N=20, out=(cost, end))
     assert ctx.device_status() == capi.SDTW_E_INVALID
     assert ctx.device_status() == capi.SDTW_OK      # cleared
-    assert cost[1].item() == -7.0 and end[1].item() == -7   # left unwritten
+    # the flagged query gets the empty query's outputs, never a stale value
+    assert cost[1].item() == float("inf") and end[1].item() == -1
     assert end[0].item() >= 0 and end[2].item() >= 0
     ctx.close()
 
@@ -208,26 +220,77 @@ def _sample(B, k, seed):
 
 
 def test_paper_batch_fp32_full_size(gpu):
-    """512 x 2,000 vs 100,000 in the bench's launch configuration; 24 sampled queries."""
+    """512 x 2,000 vs 100,000 in the bench's launch configuration: every query."""
     w = inputs.paper_fp32()
     cost, end = run_fwd(gpu, w.ref, w.queries)
     assert np.isfinite(cost).all() and (cost >= 0).all() and ((end >= 0) & (end < w.M)).all()
-    idx = _sample(w.B, 24, 1) + [int(np.nonzero(w.planted < 0)[0][0])]
-    assert parity.check_forward_f32(w.ref, w.query, idx, cost, end) == []
+    assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
 
 def test_paper_batch_i8_full_size(gpu):
+    """The integer workload at full size: all 512 queries bit-exact against the int64 oracle."""
     w = inputs.paper_i8()
     cost, end = run_fwd(gpu, w.ref, w.queries, dtype="i8")
-    idx = _sample(w.B, 24, 2)
-    assert parity.check_forward_i8(w.ref, w.query, idx, cost, end) == []
+    assert parity.check_forward_i8(w.ref, w.query, range(w.B), cost, end) == []
 
 
-def test_ragged_full_size_sampled(gpu):
-    """2,048 queries, lengths U[200, 4000], vs 1,000,000: the 12 shortest plus 2 others."""
+def _ragged_check_set(w, extra, seed):
+    """Every query of at most 400 samples (the oracle finishes those in
+    seconds against 10^6 columns) plus a few sampled longer ones."""
+    short = np.nonzero(w.lengths <= 400)[0].tolist()
+    return sorted(set(short + _sample(w.B, extra, seed)))
+
+
+def test_ragged_full_size(gpu):
+    """2,048 queries, lengths U[200, 4000], vs 1,000,000: all queries of <= 400 samples, and 3 others."""
     w = inputs.ragged_fp32()
     cost, end = run_fwd(gpu, w.ref, w.queries, offsets=w.offsets, N=int(w.lengths.max()))
     assert np.isfinite(cost).all() and ((end >= 0) & (end < w.M)).all()
-    order = np.argsort(w.lengths, kind="stable")
-    idx = sorted(set(order[:12].tolist() + _sample(w.B, 2, 3)))
+    idx = _ragged_check_set(w, 3, 3)
+    assert len(idx) >= 90
     assert parity.check_forward_f32(w.ref, w.query, idx, cost, end) == []
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_ragged_persistent_form_replays_from_a_cuda_graph(gpu, full):
+    """The ragged call captured once in a CUDA graph (the length ordering, the
+    work-counter reset and the persistent launch), replayed twice with the
+    outputs overwritten in between: bit-for-bit the eager call's results, and
+    the oracle's on checked queries.  full: the 2,048-query, 10^6-column
+    workload the bench replays (bench.py repeats the replay-equals-eager check
+    on the plan its autotuner picks)."""
+    if full:
+        w = inputs.ragged_fp32()
+    else:
+        w = inputs.ragged_fp32(B=300, n_lo=1, n_hi=900, M=40000, seed=641)
+    Nr = int(w.lengths.max())
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    offs = torch.from_numpy(w.offsets).to(gpu)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=Nr, max_total_query_len=qs.numel())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    cost = torch.empty(w.B, device=gpu)
+    end = torch.empty(w.B, dtype=torch.int64, device=gpu)
+    with torch.cuda.stream(s):
+        ctx.forward(ref, qs, offsets=offs, N=Nr, out=(cost, end), stream=s)   # eager, outside the capture
+    torch.cuda.synchronize()
+    assert ctx.device_status() == capi.SDTW_OK
+    want_c, want_e = cost.clone(), end.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ctx.forward(ref, qs, offsets=offs, N=Nr, out=(cost, end), stream=s)
+    for _ in range(2):
+        cost.fill_(float("nan"))
+        end.fill_(-7)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(cost, want_c) and torch.equal(end, want_e)
+    assert ctx.device_status() == capi.SDTW_OK
+    ctx.close()
+    c, e = cost.cpu().numpy(), end.cpu().numpy()
+    if full:
+        idx = sorted(set(np.argsort(w.lengths, kind="stable")[:6].tolist() + _sample(w.B, 2, 7)))
+    else:
+        idx = list(range(w.B))
+    assert parity.check_forward_f32(w.ref, w.query, idx, c, e) == []

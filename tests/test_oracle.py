@@ -449,3 +449,163 @@ def test_cost_of_normalised_query_gradient_matches_central_differences(oracle_mo
             assert abs(fd - gx[k]) <= 1e-5 * max(1.0, np.abs(gx).max()), (q, k, fd, gx[k])
             checked += 1
     assert checked >= 24
+
+
+# ---------------------------------------------------------------------------
+# Reference codebook (Section 8): the fit in FP64, the encoding decided in
+# float32, then the exact integer DP on the codes.
+
+def test_codebook_fit_closed_forms(oracle_mod):
+    y = np.tile([-1.0, 1.0], 500)                  # mean 0, population spread 1
+    lo, step = oracle_mod.codebook_fit(y, sigmas=4.0)
+    assert lo == -4.0 and step == 8.0 / 256.0
+    lo3, step3 = oracle_mod.codebook_fit(y, sigmas=3.0)
+    assert lo3 == -3.0 and step3 == 6.0 / 256.0
+    # a constant reference: the constant lands at code 128 with unit steps
+    assert oracle_mod.codebook_fit(np.full(7, 2.5)) == (2.5 - 128.0, 1.0)
+    # population, not sample, spread: [0, 2] has S = 1
+    assert oracle_mod.codebook_fit(np.array([0.0, 2.0]), sigmas=1.0) == (0.0, 2.0 / 256.0)
+
+
+def test_codebook_fit_is_affine_equivariant(oracle_mod):
+    y = np.cumsum(np.random.default_rng(3).standard_normal(5000))
+    lo, step = oracle_mod.codebook_fit(y)
+    lo2, step2 = oracle_mod.codebook_fit(4.0 * y - 7.0)
+    assert abs(lo2 - (4.0 * lo - 7.0)) <= 1e-9 * abs(lo2) and abs(step2 - 4.0 * step) <= 1e-12 * step2
+
+
+def test_codebook_encode_bins_and_clamps(oracle_mod):
+    lo, inv = -4.0, 32.0                            # step 1/32: bin edges exact in float32
+    k = np.arange(256)
+    edges = (lo + k / 32.0).astype(np.float32)      # a bin's lower edge belongs to it
+    centres = (lo + (k + 0.5) / 32.0).astype(np.float32)
+    assert np.array_equal(oracle_mod.codebook_encode(edges, lo, inv), k)
+    assert np.array_equal(oracle_mod.codebook_encode(centres, lo, inv), k)
+    below = np.array([-4.0001, -10.0, -1e30], dtype=np.float32)
+    above = np.array([4.0, 4.5, 1e30], dtype=np.float32)
+    assert (oracle_mod.codebook_encode(below, lo, inv) == 0).all()
+    assert (oracle_mod.codebook_encode(above, lo, inv) == 255).all()
+    # monotone, and equal to the exact floor away from bin edges
+    x = np.sort(np.random.default_rng(4).uniform(-5.0, 5.0, 20000).astype(np.float32))
+    c = oracle_mod.codebook_encode(x, lo, inv)
+    assert (np.diff(c.astype(np.int64)) >= 0).all()
+    exact = np.clip(np.floor((x.astype(np.float64) - lo) * inv), 0, 255)
+    far = np.abs((x.astype(np.float64) - lo) * inv - np.round((x.astype(np.float64) - lo) * inv)) > 1e-3
+    assert np.array_equal(c[far], exact[far].astype(np.uint8))
+
+
+def test_codebook_encode_decides_in_float32(oracle_mod):
+    # (x - lo) rounds to float32 before the product: a value just below a bin
+    # edge whose difference rounds up onto the edge takes the upper bin, as the
+    # library's float32 arithmetic does
+    lo, inv = np.float32(-3.0), np.float32(64.0)
+    x = np.nextafter(np.float32(1.0), np.float32(0.0))       # 1 - 2^-24
+    assert np.float32(x - lo) == np.float32(4.0)             # 4 - 2^-24 rounds to 4
+    assert oracle_mod.codebook_encode(np.array([x]), lo, inv)[0] == 255   # floor(256) clamped
+    x2 = np.float32(0.5) - np.float32(2.0 ** -25)            # exact: 0.5 - 2^-25
+    assert np.float32(x2 - lo) == np.float32(3.5)            # 3.5 - 2^-25 rounds to 3.5
+    # exact arithmetic would give floor(224 - 2^-19) = 223
+    assert oracle_mod.codebook_encode(np.array([x2], np.float32), lo, inv)[0] == 224
+
+
+def test_codebook_pipeline_exact_cut(oracle_mod):
+    # codes of an exact cut of the reference are the cut of the codes: cost 0 at its end
+    y = inputs.znorm(np.cumsum(np.random.default_rng(5).standard_normal(3000))).astype(np.float32)
+    lo, step = oracle_mod.codebook_fit(y)
+    lo32, inv32 = np.float32(lo), np.float32(1.0 / step)
+    cy = oracle_mod.codebook_encode(y, lo32, inv32).astype(np.int64)
+    cx = oracle_mod.codebook_encode(y[1200:1500], lo32, inv32).astype(np.int64)
+    c, e = oracle_mod.forward(cx, cy)
+    assert c == 0 and e <= 1499 and cy[e] == cx[-1]
+
+
+# ---------------------------------------------------------------------------
+# The paper's binary16 precision (Section 5.2): rounding routines pinned
+# against numpy's float16 conversion and exact rational arithmetic; the
+# binary16 DP against the int64 DP where every value is exact in binary16.
+
+def test_round_f16_matches_numpy_float16(oracle_mod):
+    rng = np.random.default_rng(21)
+    v = rng.standard_normal(200_000) * np.exp(rng.uniform(-22, 12, 200_000))
+    # exact midpoints between neighbouring binary16 values, both parities
+    h = np.float16(rng.standard_normal(5000) * 100)
+    nxt = np.nextafter(h, np.float16(np.inf))
+    mids = (h.astype(np.float64) + nxt.astype(np.float64)) / 2
+    special = np.array([65504.0, 65519.99, 65520.0, -65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26, 0.0, -0.0])
+    for arr in (v, mids, special):
+        with np.errstate(over="ignore"):
+            want = arr.astype(np.float16).astype(np.float64)
+        got = oracle_mod.round_f16(arr)
+        assert np.array_equal(got, want) and np.array_equal(np.signbit(got), np.signbit(want))
+
+
+def _f16_nearest(fr):
+    """The binary16 value nearest to the Fraction fr (ties to even), by exact
+    comparison with the two neighbours that bracket it."""
+    from fractions import Fraction
+    lo = np.float16(float(fr))
+    if Fraction(float(lo)) > fr:
+        lo = np.nextafter(lo, np.float16(-np.inf))
+    hi = np.nextafter(lo, np.float16(np.inf))
+    dl, dh = fr - Fraction(float(lo)), Fraction(float(hi)) - fr
+    if dl < dh:
+        return float(lo)
+    if dh < dl:
+        return float(hi)
+    return float(lo) if (lo.view(np.uint16) & 1) == 0 else float(hi)
+
+
+def test_fma_f16_is_correctly_rounded(oracle_mod):
+    from fractions import Fraction
+    rng = np.random.default_rng(22)
+    a = np.float16(rng.standard_normal(3000) * 30)
+    c = np.float16(rng.standard_normal(3000) * 1000)
+    c[:500] = np.float16(rng.standard_normal(500) * 1e-3)         # small addends
+    # products that land exactly on midpoints once an addend is added
+    a[500:800] = np.float16(rng.integers(1, 64, 300) * 0.5)
+    c[500:800] = np.float16(0.25)
+    got = oracle_mod.fma_f16(a, a, c)
+    for k in range(len(a)):
+        exact = Fraction(float(a[k])) * Fraction(float(a[k])) + Fraction(float(c[k]))
+        assert got[k] == _f16_nearest(exact), (a[k], c[k], got[k])
+
+
+def test_f16_dp_equals_int_dp_when_exact(oracle_mod):
+    # small integer samples: every local cost and every D stays an integer
+    # below 2048, exact in binary16, so the binary16 DP is the exact DP
+    rng = np.random.default_rng(23)
+    for _ in range(20):
+        n, m = int(rng.integers(1, 12)), int(rng.integers(1, 40))
+        x = rng.integers(-3, 4, n)
+        y = rng.integers(-3, 4, m)
+        c16, e16, row16 = oracle_mod.forward_f16(x.astype(np.float16), y.astype(np.float16), last_row=True)
+        ci, ei = oracle_mod.forward(x.astype(np.int64), y.astype(np.int64))
+        assert c16 == ci and e16 == ei and np.all(row16 < 2048)
+
+
+def test_f16_dp_rounds_every_operation(oracle_mod):
+    # one row and one column: D = fl16(d * d) with d = fl16(x - y); a case
+    # where the subtraction itself rounds (1000 - 0.3 is not a binary16 value)
+    x = np.array([1000.0], dtype=np.float16)
+    y = np.array([0.3], dtype=np.float16)
+    d = oracle_mod.round_f16(1000.0 - float(y[0]))
+    c, e = oracle_mod.forward_f16(x, y)
+    assert d != 1000.0 - float(y[0]) and c == oracle_mod.round_f16(d * d)[()] and e == 0
+    # large costs overflow to +inf, as binary16 does
+    c, e = oracle_mod.forward_f16(np.array([200.0] * 3, np.float16), np.array([-60.0], np.float16))
+    assert c == np.inf and e == 0
+
+
+def test_f16_dp_close_to_f64_on_paper_shaped_inputs(oracle_mod):
+    # the binary16 cost of a z-normalised query against a z-normalised
+    # reference stays within a few binary16 units of the FP64 cost of the
+    # same (binary16) samples: each cell adds at most half a unit at its scale
+    w = inputs.tiny(B=4, N=64, M=900, seed=24)
+    for q in range(w.B):
+        x = w.query(q).astype(np.float16)
+        y = w.ref.astype(np.float16)
+        c16, _ = oracle_mod.forward_f16(x, y)
+        c64, _ = oracle_mod.forward(x.astype(np.float64), y.astype(np.float64))
+        assert abs(c16 - c64) <= 64 * 2.0 ** -11 * max(c64, 1.0) * 2
+    with pytest.raises(ValueError):
+        oracle_mod.forward_f16(np.array([0.1]), np.array([0.2]))        # not binary16 values

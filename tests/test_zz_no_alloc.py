@@ -73,6 +73,30 @@ def test_noalloc_int8_matches_forward_twice(gpu):
         assert torch.equal(cost.cpu(), c_ref.cpu()) and torch.equal(end.cpu(), e_ref.cpu())
 
 
+def test_noalloc_over_long_query_gets_the_empty_outputs(gpu):
+    # a ragged query longer than N cannot be reported (no context): it gets the
+    # empty query's outputs, and the others are computed as by sdtw_forward
+    lengths = np.array([20, 90, 0, 35], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    rng = np.random.default_rng(614)
+    ref = torch.from_numpy(rng.standard_normal(3000).astype(np.float32)).to(gpu)
+    flat = torch.from_numpy(rng.standard_normal(int(offs[-1])).astype(np.float32)).to(gpu)
+    o = torch.from_numpy(offs).to(gpu)
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        cost = torch.full((4,), -1.0, device=gpu)
+        end = torch.full((4,), -7, dtype=torch.int64, device=gpu)
+        st = capi.sdtw_forward_noalloc(capi.SDTW_F32, ref.data_ptr(), 3000, flat.data_ptr(), o.data_ptr(), 4, 40,
+                                       cost.data_ptr(), end.data_ptr(), s)
+        assert st == capi.SDTW_OK
+        torch.cuda.synchronize()
+        c, e = cost.cpu().numpy(), end.cpu().numpy()
+        for q in (1, 2):
+            assert np.isinf(c[q]) and c[q] > 0 and e[q] == -1
+        fl = flat.cpu().numpy()
+        assert parity.check_forward_f32(ref.cpu().numpy(), lambda q: fl[offs[q]:offs[q + 1]], [0, 3], c, e) == []
+
+
 def test_noalloc_rejects_batches_over_its_maximum(gpu):
     z = torch.zeros(8, device=gpu)
     s = torch.cuda.current_stream().cuda_stream
