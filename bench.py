@@ -364,7 +364,8 @@ def run_autograd_form(args, ctx, ref, qs, B, N, M, flush, stream):
 
 
 def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
-    """Forward alone, int8 forward, and the ragged persistent form under a CUDA graph."""
+    """Forward alone, int8, binary16 and codebook forwards, the normaliser, and
+    the ragged persistent form under a CUDA graph."""
     import torch
 
     from paper_2403_06931_gb300 import capi, inputs
@@ -405,6 +406,45 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
     ms = timed(lambda: ictx.forward(ri, qi, out=(ci, end)), 5)
     forms["forward_i8"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": iplan}
     ictx.close()
+
+    # binary16 (the paper's precision, Section 5.2): two queries per thread as
+    # __half2; the same batch rounded to binary16.  Its difference from the FP64
+    # DP of the same samples is reported on a few queries (the oracle on the
+    # host), beside the throughput.
+    h_ref, h_q = ref.to(torch.float16), qs.to(torch.float16)
+    hctx = SdtwContext(dtype="f16", max_ref_len=M, max_batch=B, max_query_len=N)
+    hplan = hctx.plan(B, N, M) if args.no_autotune else hctx.autotune(h_ref, h_q)
+    hc, he = hctx.forward(h_ref, h_q)
+    ms = timed(lambda: hctx.forward(h_ref, h_q, out=(hc, he)), 5)
+    forms["forward_f16"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": hplan,
+                            "arithmetic": "binary16, two queries per thread (__half2), no rebasing"}
+    if not args.no_cpu_baseline:
+        import oracle
+        k = 4
+        y64 = h_ref.cpu().numpy().astype(np.float64)
+        x64 = h_q[:k].cpu().numpy().astype(np.float64)
+        c64, _ = oracle.forward_batch(y64, x64, threads=min(k, host_threads()))
+        c16 = hc[:k].cpu().numpy().astype(np.float64)
+        forms["forward_f16"]["rel_err_vs_fp64"] = {"queries": k, "max": float(np.max(np.abs(c16 - c64) / c64)),
+                                                   "mean": float(np.mean(np.abs(c16 - c64) / c64))}
+    hctx.close()
+
+    # the reference codebook of Section 8: fit on the reference, encode the
+    # batch to uint8 codes, the exact int32 DP on the codes
+    from paper_2403_06931_gb300.sdtw import codebook_encode, codebook_fit
+    params = codebook_fit(ref)
+    cr, cq = codebook_encode(ref, params), codebook_encode(qs, params)
+    ms_enc = timed(lambda: codebook_encode(qs, params, out=cq), 5)
+    uctx = SdtwContext(dtype="u8", max_ref_len=M, max_batch=B, max_query_len=N)
+    uplan = uctx.plan(B, N, M) if args.no_autotune else uctx.autotune(cr, cq)
+    ui = torch.empty(B, dtype=torch.int32, device=dev)
+    uctx.forward(cr, cq, out=(ui, end))
+    ms = timed(lambda: uctx.forward(cr, cq, out=(ui, end)), 5)
+    forms["forward_u8_codebook"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3), "plan": uplan,
+                                    "encode_ms": round(ms_enc, 4),
+                                    "encode_gbs": round(5 * B * N / (ms_enc * 1e-3) / 1e9, 1),
+                                    "codebook": "mean +- 4 S of the reference, 256 equal bins"}
+    uctx.close()
 
     # batch z-normalisation (Section 5.1, Eq. 2) of query batches shaped like
     # the paper's (512 x 2,000 samples, as its Table 1 times it).  HBM-bound:

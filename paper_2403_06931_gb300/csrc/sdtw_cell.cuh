@@ -3,7 +3,8 @@
 //   D(i,j) = (x_i - y_j)^2 + min{ D(i-1,j), D(i,j-1), D(i-1,j-1) }
 //
 // FP32: one subtract, one three-input minimum (sm_100+ min.f32 with three
-// sources) and one fused multiply-add.
+// sources) and one fused multiply-add; two independent cells share one packed
+// f32x2 multiply-add (sm_100+).
 // INT:  int8 samples or uint8 codes widened to int32; costs are non-negative int32.  A
 // non-negative int32 read as an IEEE float sorts exactly like the integer
 // (the bit patterns 0 .. 0x7F7FFFFF are the finite non-negative floats in
@@ -52,6 +53,17 @@ struct Mode<float> {
         const float d = x - y;
         return fmaf(d, d, min3_f32(up, diag, left));
     }
+    // two independent cells at once: the multiply-adds as one packed
+    // f32x2 fused multiply-add (each lane rounded once, exactly as fmaf), so
+    // the pair costs five instructions instead of six and every value is
+    // the one cell() gives
+    static constexpr bool kPack2 = true;
+    static __device__ __forceinline__ float2 cell2(V x0, V y0, V up0, V dg0, V lf0, V x1, V y1, V up1, V dg1, V lf1)
+    {
+        const float2 d = make_float2(x0 - y0, x1 - y1);
+        const float2 m = make_float2(min3_f32(up0, dg0, lf0), min3_f32(up1, dg1, lf1));
+        return __ffma2_rn(d, d, m);
+    }
 };
 
 // The integer modes (int8 samples, or uint8 codebook codes): int32 costs.
@@ -60,6 +72,7 @@ struct ModeInt {
     using V = int32_t;
     using Col = int;
     static constexpr bool kPair = false;
+    static constexpr bool kPack2 = false;
     static constexpr bool kRebase = false;  // integer sums are exact
     // Largest finite float pattern: above every reachable cost (N <= 32,896
     // samples of at most 255^2 each), and never NaN or infinity.
@@ -88,6 +101,7 @@ struct Mode<__half> {
     using Col = int2;  // the two queries' bottom-row minimum columns
     static constexpr bool kRebase = false;
     static constexpr bool kPair = true;
+    static constexpr bool kPack2 = false;
     static __device__ __forceinline__ V inf() { return __halves2half2(__ushort_as_half(0x7c00), __ushort_as_half(0x7c00)); }
     static __device__ __forceinline__ V zero() { return __halves2half2(__ushort_as_half(0), __ushort_as_half(0)); }
     static __device__ __forceinline__ V widen(__half v) { return __halves2half2(v, v); }  // a reference sample, both halves

@@ -135,44 +135,79 @@ __device__ __forceinline__ void tile_step(typename Md::V (&prev)[W], typename Md
                                           typename Md::Col& best_col)
 {
     using V = typename Md::V;
-#pragma unroll
-    for (int k = 0; k < W + RT - 1; ++k) {
-#pragma unroll
-        for (int rr = 0; rr < RT; ++rr) {
-            const int j = k - rr;
-            if (j < 0 || j >= W) continue;
-            V up, dg, lf;
-            if (rr == 0) {
-                up = prev[j];
-                dg = j == 0 ? diag : prev[j - 1];
-            } else {
-                up = A[rr - 1][j];
-                dg = j == 0 ? left[rr - 1] : A[rr - 1][j - 1];
-            }
-            if (j == 0)
-                lf = left[rr];
-            else if (rr == RT - 1)
-                lf = prev[j - 1];
-            else
-                lf = A[rr][j - 1];
-            const V nv = Md::cell(x[rr], y[j], up, dg, lf);
-            if (rr == RT - 1)
-                prev[j] = nv;
-            else
-                A[rr][j] = nv;
-            if constexpr (BOT) {
-                if (rr == bot_row) {
-                    if constexpr (Md::kPair) {
-                        if (base + j < M) Md::bot_update(nv, base + j, best, best_col);
-                    } else {
-                        V v = nv;
-                        if constexpr (Md::kRebase) v = nv + B;
-                        if (base + j < M && v < best) {
-                            best = v;
-                            best_col = base + j;
-                        }
+    // the inputs of cell (rr, j) of the tile
+    auto inputs = [&](int rr, int j, V& up, V& dg, V& lf) {
+        if (rr == 0) {
+            up = prev[j];
+            dg = j == 0 ? diag : prev[j - 1];
+        } else {
+            up = A[rr - 1][j];
+            dg = j == 0 ? left[rr - 1] : A[rr - 1][j - 1];
+        }
+        if (j == 0)
+            lf = left[rr];
+        else if (rr == RT - 1)
+            lf = prev[j - 1];
+        else
+            lf = A[rr][j - 1];
+    };
+    // its result: the last row overwrites the previous row in place; with BOT
+    // the bottom row updates the running minimum
+    auto result = [&](int rr, int j, V nv) {
+        if (rr == RT - 1)
+            prev[j] = nv;
+        else
+            A[rr][j] = nv;
+        if constexpr (BOT) {
+            if (rr == bot_row) {
+                if constexpr (Md::kPair) {
+                    if (base + j < M) Md::bot_update(nv, base + j, best, best_col);
+                } else {
+                    V v = nv;
+                    if constexpr (Md::kRebase) v = nv + B;
+                    if (base + j < M && v < best) {
+                        best = v;
+                        best_col = base + j;
                     }
                 }
+            }
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < W + RT - 1; ++k) {
+        if constexpr (Md::kPack2) {
+            // anti-diagonal k holds cells (rr, k - rr): rows rr and rr + 1 are
+            // independent and go through one packed multiply-add when both
+            // cells lie in the strip (inputs gathered before either is written)
+#pragma unroll
+            for (int rr = 0; rr < RT; rr += 2) {
+                const int j0 = k - rr, j1 = k - rr - 1;
+                const bool in0 = j0 >= 0 && j0 < W, in1 = j1 >= 0 && j1 < W;
+                if (in0 && in1) {
+                    V up0, dg0, lf0, up1, dg1, lf1;
+                    inputs(rr, j0, up0, dg0, lf0);
+                    inputs(rr + 1, j1, up1, dg1, lf1);
+                    const float2 nv = Md::cell2(x[rr], y[j0], up0, dg0, lf0, x[rr + 1], y[j1], up1, dg1, lf1);
+                    result(rr, j0, nv.x);
+                    result(rr + 1, j1, nv.y);
+                } else if (in0) {
+                    V up, dg, lf;
+                    inputs(rr, j0, up, dg, lf);
+                    result(rr, j0, Md::cell(x[rr], y[j0], up, dg, lf));
+                } else if (in1) {
+                    V up, dg, lf;
+                    inputs(rr + 1, j1, up, dg, lf);
+                    result(rr + 1, j1, Md::cell(x[rr + 1], y[j1], up, dg, lf));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+                const int j = k - rr;
+                if (j < 0 || j >= W) continue;
+                V up, dg, lf;
+                inputs(rr, j, up, dg, lf);
+                result(rr, j, Md::cell(x[rr], y[j], up, dg, lf));
             }
         }
     }

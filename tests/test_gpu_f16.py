@@ -5,7 +5,8 @@ subtraction, then one fused multiply-add); the GPU packs two queries per
 thread as __half2 and must return the same binary16 cost (widened exactly to
 float) and the same end column, bit for bit.  Against the FP64 DP of the same
 binary16 samples the difference is what binary16 arithmetic makes of a long
-sum; a loose bound is checked and the error reported by bench.py.
+sum (tens of percent on paper-shaped inputs); only a sanity bound is checked
+and bench.py reports the error.
 """
 from concurrent.futures import ThreadPoolExecutor
 
@@ -82,8 +83,11 @@ def test_ragged_batches_are_unsupported(gpu):
 
 def test_paper_batch_full_size_sampled(gpu):
     """512 x 2,000 vs 100,000 in binary16: 24 sampled queries (and their pair
-    partners) bit-exact against the binary16 oracle; the difference from the
-    FP64 DP of the same samples stays within a percent of the cost."""
+    partners) bit-exact against the binary16 oracle.  Against the FP64 DP of
+    the same samples binary16 is far off on this workload -- once D passes
+    about 256 a local cost below half a binary16 unit (0.125) rounds away, so
+    the sum under-counts -- and only a sanity bound is checked here (bench.py
+    reports the error)."""
     w = inputs.paper_fp32()
     q16 = w.queries.astype(np.float16)
     y16 = w.ref.astype(np.float16)
@@ -95,4 +99,4 @@ def test_paper_batch_full_size_sampled(gpu):
     assert check_f16(y16, q16, idx, cost, end) == []
     c64, _ = oracle.forward_batch(y16.astype(np.float64), q16.astype(np.float64), indices=idx[:8])
     rel = np.abs(cost[idx[:8]] - c64) / c64
-    assert rel.max() < 1e-2
+    assert rel.max() < 1.0
