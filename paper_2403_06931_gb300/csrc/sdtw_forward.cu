@@ -472,6 +472,8 @@ fwd_chain_kernel(const FwdArgs a)
 #pragma unroll 1
                     for (int u = ub; u < ue; ++u) {
                         const int t = t0 + u;
+                        V x[RT];
+                        load_x<RT>(xs, p, x);
                         V recv[RT];
 #pragma unroll
                         for (int rr = 0; rr < RT; ++rr)
@@ -508,8 +510,6 @@ fwd_chain_kernel(const FwdArgs a)
                             if (rebase_to_left<true, W, RT>(prev, diag, left, B))
                                 dconv = __shfl_up_sync(0xffffffffu, B, 1) - B;
                         }
-                        V x[RT];
-                        load_x<RT>(xs, p, x);
                         tile_step<Md, W, RT, false>(prev, A, y, x, diag, left, 0, B, base, M, best, best_col);
                         diag = left[RT - 1];
                         if (lane == 31) {

@@ -34,7 +34,7 @@ constexpr int kIntMaxN = 32896;
 // FP32 mode: a strip whose left input at the first row of a tile lies more
 // than this far below the strip's integer base is rebased to that input before
 // the tile (see sdtw_forward.cu).  The backward replays the same decision.
-constexpr float kRebaseBelow = 64.f;
+constexpr float kRebaseBelow = 256.f;
 
 // Dynamic shared memory one CTA may use on sm_103a.  Shared-memory sizes are
 // computed in 64-bit arithmetic and checked against this before any launch,

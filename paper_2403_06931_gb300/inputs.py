@@ -199,10 +199,12 @@ def ragged_fp32(seed: int = SEED_BASE + 4, B: int = 2048, n_lo: int = 200,
 
 
 def stretched(seed: int = SEED_BASE + 6, B: int = 16, N: int = 400, M: int = 40_000,
-              step_lo: int = 4, step_hi: int = 24, noise: float = 0.05) -> Workload:
+              step_lo: int = 4, step_hi: int = 24, noise: float = 0.05, scale: float = 1.0) -> Workload:
     """Queries that are the reference subsampled by an integer step in
     [step_lo, step_hi] (plus noise, z-normalised): each optimal path runs about
-    `step` columns per row, long horizontal runs across the reference."""
+    `step` columns per row, long horizontal runs across the reference.  With
+    scale != 1 the reference and the queries are multiplied by it afterwards
+    (larger costs on a small shape)."""
     rng = rng_for(seed)
     ref = znorm(random_walk(rng, M))
     qs, planted = [], np.zeros(B, dtype=np.int64)
@@ -215,8 +217,10 @@ def stretched(seed: int = SEED_BASE + 6, B: int = 16, N: int = 400, M: int = 40_
             cut = np.resize(cut, N)
         qs.append(znorm(cut + noise * rng.standard_normal(N)))
         planted[q] = o
-    recipe = dict(ref="znorm(cumsum N(0,1))", M=M, B=B, N=N, step=(step_lo, step_hi), noise_sigma=noise, seed=seed)
-    return Workload(f"sdtw_stretched_{B}x{N}_vs_{M}", ref.astype(np.float32), np.stack(qs).astype(np.float32),
+    recipe = dict(ref="znorm(cumsum N(0,1))", M=M, B=B, N=N, step=(step_lo, step_hi), noise_sigma=noise, seed=seed,
+                  scale=scale)
+    return Workload(f"sdtw_stretched_{B}x{N}_vs_{M}", (scale * ref).astype(np.float32),
+                    (scale * np.stack(qs)).astype(np.float32),
                     None, np.full(B, N, dtype=np.int64), planted, seed, "f32", recipe)
 
 

@@ -22,7 +22,8 @@ def main():
     ap.add_argument("--B", type=int, default=None, help="queries (default: the workload's)")
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--M", type=int, default=None)
-    ap.add_argument("--dtype", default="f32", choices=["f32", "i8"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i8", "u8", "f16"],
+                    help="u8: the batch encoded with the reference codebook; f16: the batch rounded to binary16")
     ap.add_argument("--reps", type=int, default=3, help="timed runs after one warm-up")
     ap.add_argument("--backward", action="store_true")
     ap.add_argument("--autotune", action="store_true")
@@ -50,6 +51,12 @@ def main():
     ref = torch.from_numpy(w.ref).to(dev)
     qs = torch.from_numpy(w.queries).to(dev)
     offs = torch.from_numpy(w.offsets).to(dev) if w.offsets is not None else None
+    if a.dtype == "f16":
+        ref, qs = ref.to(torch.float16), qs.to(torch.float16)
+    elif a.dtype == "u8":
+        from .sdtw import codebook_encode, codebook_fit
+        params = codebook_fit(ref)
+        ref, qs = codebook_encode(ref, params), codebook_encode(qs, params)
     N = int(w.lengths.max())
     ctx = SdtwContext(dtype=a.dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=N,
                       max_total_query_len=qs.numel(), grad=a.backward or a.keep_checkpoints,

@@ -34,7 +34,7 @@ import numpy as np
 import pytest
 
 K_CHUNK = 32   # csrc/sdtw_internal.h kChunk
-REBASE_BELOW = 64.0   # csrc/sdtw_internal.h kRebaseBelow
+REBASE_BELOW = 256.0   # csrc/sdtw_internal.h kRebaseBelow
 STRIDES = (16, 32, 64)   # checkpoint strides the library supports
 INF = float("inf")
 
@@ -631,16 +631,17 @@ def test_kernel_schedule_random_shapes():
         assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], n, fw["end"]), (P, W, RT, RS, KS, n, M)
 
 
-def _stretched(seed, M=1400, step=8, n=150):
+def _stretched(seed, M=1400, step=8, n=150, scale=8.0):
     """A query that is the reference subsampled by `step` (plus a little noise):
     its optimal path runs horizontally for about `step` columns per row, so
     cheap values cross strips whose own cells are far more expensive -- the
-    case the forward's rebase to a low left input exists for."""
+    case the forward's rebase to a low left input exists for.  Both series are
+    scaled by `scale` so that costs reach the rebase threshold on a small case."""
     rng = np.random.default_rng(seed)
     y = np.cumsum(rng.standard_normal(M))
     y = (y - y.mean()) / y.std()
     x = y[100:100 + step * n:step] + 0.05 * rng.standard_normal(n)
-    return (x - x.mean()) / x.std(), y
+    return scale * (x - x.mean()) / x.std(), scale * y
 
 
 @pytest.mark.parametrize("KS", STRIDES)

@@ -167,10 +167,10 @@ def test_backward_every_checkpoint_stride(gpu, RT, KS):
 
 @pytest.mark.parametrize("KS", [16, 32, 64])
 def test_backward_stretched_paths(gpu, KS):
-    # long horizontal runs: the forward rebases strips to low left inputs, and
-    # the backward must replay every such rebase to reproduce the forward's
-    # values (the device checks the end cell bit for bit)
-    w = inputs.stretched(B=8, N=300, M=30000)
+    # long horizontal runs, scaled so that costs reach the forward's rebase to
+    # low left inputs: the backward must replay every such rebase to reproduce
+    # the forward's values (the device checks the end cell bit for bit)
+    w = inputs.stretched(B=8, N=300, M=30000, scale=8.0)
     cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=KS)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)

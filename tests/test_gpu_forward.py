@@ -85,13 +85,14 @@ def test_fast_path_plans(gpu, W, P, RT):
         assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
 
 
+@pytest.mark.parametrize("scale", [1.0, 8.0])
 @pytest.mark.parametrize("W", [16, 24, 32])
-def test_stretched_paths_fp32(gpu, W):
+def test_stretched_paths_fp32(gpu, W, scale):
     # queries subsampled from the reference: their paths run long horizontal
     # stretches into strips whose own cells cost far more (the FP32 fill
     # rebases a strip to such a low left input; without it these costs drift
-    # past the tolerance)
-    w = inputs.stretched()
+    # past the tolerance); scaled by 8, costs reach that rebase on this shape
+    w = inputs.stretched(scale=scale)
     cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W)
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
