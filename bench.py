@@ -49,12 +49,14 @@ FWD_SRC_SHA = "2e1ac1a31cedb5f3"
 FWD_TRAFFIC_BYTES = 4 * (2_072_064 + 1_362_158_080)
 
 
-def src_sha(path):
-    """Hash of a CUDA source's code: comments and blank lines do not count, so
+def src_sha(*paths):
+    """Hash of CUDA sources' code: comments and blank lines do not count, so
     a comment edit keeps counters taken on the kernel valid."""
     import re
-    with open(path) as f:
-        text = f.read()
+    text = ""
+    for path in paths:
+        with open(path) as f:
+            text += f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     lines = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
     code = "\n".join(ln for ln in lines if ln.strip())
@@ -287,8 +289,9 @@ def run_ours(args, rank, world, local_rank):
     peak_gcups = sms * LANES_PER_SM * f_max * 1e6 / OPS_PER_CELL / 1e9
     fwd_avg = sum(fwd_ms) / len(fwd_ms)
     achieved = cells / (fwd_avg * 1e-3) / 1e9
-    fwd_src = os.path.join(ROOT, "paper_2403_06931_gb300", "csrc", "sdtw_forward.cu")
-    traffic = FWD_TRAFFIC_BYTES if FWD_SRC_SHA == src_sha(fwd_src) else None
+    csrc = os.path.join(ROOT, "paper_2403_06931_gb300", "csrc")
+    fwd_sha = src_sha(os.path.join(csrc, "sdtw_fill.cuh"), os.path.join(csrc, "sdtw_cell.cuh"))
+    traffic = FWD_TRAFFIC_BYTES if FWD_SRC_SHA == fwd_sha else None
     roof = {"bound": "alu", "kernel": "fwd_chain_kernel", "achieved": round(achieved, 1),
             "peak": round(peak_gcups, 1), "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4),
             "traffic": traffic,
@@ -445,6 +448,16 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
                                     "encode_gbs": round(5 * B * N / (ms_enc * 1e-3) / 1e9, 1),
                                     "codebook": "mean +- 4 S of the reference, 256 equal bins"}
     uctx.close()
+    # early-INF pruning (Section 8, opt-in, changes results): cells whose codes
+    # differ by more than 32 (one standard deviation of the reference) cost +inf
+    pctx = SdtwContext(dtype="u8", max_ref_len=M, max_batch=B, max_query_len=N, prune_gap=32)
+    pplan = pctx.plan(B, N, M) if args.no_autotune else pctx.autotune(cr, cq)
+    pctx.forward(cr, cq, out=(ui, end))
+    ms = timed(lambda: pctx.forward(cr, cq, out=(ui, end)), 5)
+    forms["forward_u8_codebook_pruned"] = {"gcups": round(cells / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 3),
+                                           "plan": pplan, "prune_gap": 32,
+                                           "queries_with_no_path": int((end < 0).sum().item())}
+    pctx.close()
 
     # batch z-normalisation (Section 5.1, Eq. 2) of query batches shaped like
     # the paper's (512 x 2,000 samples, as its Table 1 times it).  HBM-bound:
@@ -488,7 +501,14 @@ def run_forms(args, ctx, w, ref, qs, cost, end, flush, stream, dev):
         cr = torch.empty(wr.B, device=dev)
         er = torch.empty(wr.B, dtype=torch.int64, device=dev)
         rctx = SdtwContext(max_ref_len=wr.M, max_batch=wr.B, max_query_len=Nr, max_total_query_len=qr.numel())
-        rplan = rctx.plan(wr.B, Nr, wr.M, ragged=True) if args.no_autotune else rctx.autotune(rr, qr, offsets=orr, N=Nr)
+        if args.no_autotune:
+            rplan = rctx.plan(wr.B, Nr, wr.M, ragged=True)
+        else:
+            # tuned on the first 512 queries: the same shape class (ragged, the
+            # same length and reference-size buckets) at a quarter of the time
+            nt = min(512, wr.B)
+            rplan = rctx.autotune(rr, qr, offsets=orr[:nt + 1], N=Nr)
+            rplan = rctx.plan(wr.B, Nr, wr.M, ragged=True)
         rctx.forward(rr, qr, offsets=orr, N=Nr, out=(cr, er))
         torch.cuda.synchronize()
         eager_c, eager_e = cr.clone(), er.clone()

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SDTW_ABI_VERSION 3
+#define SDTW_ABI_VERSION 4
 
 typedef struct sdtw_ctx sdtw_ctx;
 
@@ -98,7 +98,10 @@ typedef struct sdtw_config {
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
     int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints: 16, 32 or 64; 0 = chosen by
                                     the library (16, or the autotuner's choice) */
-    int32_t reserved0;           /* must be 0 */
+    int32_t prune_gap;           /* SDTW_I8 / SDTW_U8 only: 0 = off (exact); > 0 = early-INF pruning (paper
+                                    Section 8, opt-in, changes results): a cell whose two samples differ by more
+                                    than prune_gap costs +inf, and +inf absorbs every sum; a query with no path
+                                    left gets cost INT32_MAX and end -1 */
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
     uint64_t spin_limit;         /* reserved: no kernel of this build waits on a flag; must be 0 */
     uint32_t flags;              /* SDTW_FLAG_* */
@@ -138,7 +141,8 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * *out receives the context, or NULL on error.
  * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
  * SDTW_FLAG_GRAD with SDTW_I8, an unsupported seg_width or tile_rows, a
- * non-zero reserved0 or spin_limit, a negative ckpt_stride),
+ * non-zero spin_limit, a negative ckpt_stride or prune_gap, a prune_gap with
+ * SDTW_F32 or SDTW_F16),
  * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 16, 32 or 64, or a
  * max_query_len no forward plan can stage in shared memory),
  * SDTW_E_NOMEM (workspace above mem_cap_bytes, too small for one query's
@@ -151,17 +155,20 @@ sdtw_status sdtw_destroy(sdtw_ctx* ctx);
 
 /*
  * Forward sDTW of a batch (Section 2, Eq. 1; batch layout of Section 5).
- *   ref      device, M elements: float (SDTW_F32) or int8 (SDTW_I8).
+ *   ref      device, M elements: float (SDTW_F32), int8 (SDTW_I8), uint8 codebook
+ *            codes (SDTW_U8) or IEEE binary16 (SDTW_F16).
  *   queries  device: uniform batch [B][N] row-major when offsets == NULL;
  *            ragged batch of offsets[B] elements when offsets != NULL
  *            (query q = queries[offsets[q] .. offsets[q+1])).  Same element
  *            type as ref.
  *   offsets  device int64 [B+1], non-decreasing, offsets[0] = 0, or NULL.
  *            Ragged queries must be no longer than N; an empty query returns
- *            cost = +inf (SDTW_F32) or INT32_MAX (SDTW_I8) and end = -1.
+ *            cost = +inf (SDTW_F32) or INT32_MAX (SDTW_I8, SDTW_U8) and end = -1.
+ *            SDTW_F16 takes uniform batches only (offsets must be NULL).
  *   B        number of queries (0 is a no-op).  N: the query length (uniform)
  *            or an upper bound on every query length (ragged).  M >= 1.
- *   cost     device, B elements: float (SDTW_F32) or int32 (SDTW_I8).
+ *   cost     device, B elements: float (SDTW_F32; SDTW_F16, holding the binary16
+ *            result exactly) or int32 (SDTW_I8, SDTW_U8).
  *   end      device int64, B elements: the smallest column of the minimum.
  * With SDTW_FLAG_KEEP_CHECKPOINTS the call also stores the checkpoints a
  * following sdtw_backward (or sdtw_path) on the same arguments reuses, when
@@ -169,7 +176,8 @@ sdtw_status sdtw_destroy(sdtw_ctx* ctx);
  * backward re-runs the forward in chunks of queries).
  * Errors: SDTW_E_INVALID (null pointers with B > 0, N < 1, M < 1, sizes above
  * the context maxima; SDTW_I8 and SDTW_U8 need N <= 32,896 so int32 costs cannot
- * overflow), SDTW_E_UNSUPPORTED (N too long for shared memory), SDTW_E_CUDA.
+ * overflow), SDTW_E_UNSUPPORTED (N too long for shared memory, offsets with
+ * SDTW_F16), SDTW_E_CUDA.
  */
 sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* queries,
                          const int64_t* offsets, int32_t B, int32_t N, void* cost, int64_t* end,
@@ -341,8 +349,9 @@ sdtw_status sdtw_codebook_encode(const float* in, int64_t n, const float* params
  * query, 4 query rows per thread per step); its only scratch (work counter, status word, query order) is one
  * fixed-size array in the library's device memory, which every GPU that
  * loads the library keeps until the process exits.
- *   dtype     SDTW_F32 or SDTW_I8; ref, queries, offsets, B, N, M, cost and
- *             end as in sdtw_forward (device pointers owned by the caller).
+ *   dtype     SDTW_F32, SDTW_I8, SDTW_U8 or SDTW_F16 (uniform batches only);
+ *             ref, queries, offsets, B, N, M, cost and end as in sdtw_forward
+ *             (device pointers owned by the caller); no pruning.
  *   stream    the launch stream; the device is the calling thread's current
  *             device.
  * The first call on a device looks up the scratch array's device address
@@ -352,10 +361,10 @@ sdtw_status sdtw_codebook_encode(const float* in, int64_t n, const float* params
  * issued.  Each call clears the counter and status word itself.  Errors found
  * on the device are not reported (there is no context to read them from): a
  * ragged query longer than N gets the empty query's outputs (cost = +inf, or
- * INT32_MAX in SDTW_I8; end = -1).
+ * INT32_MAX in the integer modes; end = -1).
  * Errors: SDTW_E_INVALID (bad sizes or null pointers as for sdtw_forward,
  * unknown dtype, B > SDTW_NOALLOC_MAX_BATCH), SDTW_E_UNSUPPORTED (N too long
- * for shared memory), SDTW_E_CUDA.
+ * for shared memory, offsets with SDTW_F16), SDTW_E_CUDA.
  */
 sdtw_status sdtw_forward_noalloc(sdtw_dtype dtype, const void* ref, int64_t M, const void* queries,
                                  const int64_t* offsets, int32_t B, int32_t N, void* cost, int64_t* end,

@@ -63,9 +63,11 @@ def _load():
             lib.sdtw_oracle_forward_f16.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, _d, _i, _d]
             lib.sdtw_oracle_round_f16.argtypes = [_d, ctypes.c_int64, _d]
             lib.sdtw_oracle_fma_f16.argtypes = [_d, _d, _d, ctypes.c_int64, _d]
+            lib.sdtw_oracle_forward_pruned_i64.argtypes = [_i, ctypes.c_int64, _i, ctypes.c_int64, ctypes.c_int64,
+                                                           _i, _i]
             for f in (lib.sdtw_oracle_forward_f64, lib.sdtw_oracle_forward_i64, lib.sdtw_oracle_walkback_f64,
                       lib.sdtw_oracle_znorm_f64, lib.sdtw_oracle_forward_f16, lib.sdtw_oracle_round_f16,
-                      lib.sdtw_oracle_fma_f16):
+                      lib.sdtw_oracle_fma_f16, lib.sdtw_oracle_forward_pruned_i64):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -105,6 +107,25 @@ def forward(x, y, last_row: bool = False):
     if rc != 0:
         raise ValueError(f"oracle forward failed (code {rc}) for n={np.size(x)}, m={np.size(y)}")
     return (c.value, e.value, row) if last_row else (c.value, e.value)
+
+
+PRUNED_INF = 1 << 62   # the pruned oracle's +inf
+
+
+def forward_pruned(x, y, gap: int):
+    """Integer sDTW with the early-INF pruning of Section 8: a cell whose
+    samples differ by more than gap costs +inf, and +inf absorbs every sum.
+    Returns (cost, end); cost PRUNED_INF and end -1 when every last-row cell
+    is pruned away."""
+    xv = np.ascontiguousarray(x, dtype=np.int64)
+    yv = np.ascontiguousarray(y, dtype=np.int64)
+    c = ctypes.c_int64()
+    e = ctypes.c_int64()
+    rc = _load().sdtw_oracle_forward_pruned_i64(_p(xv, _i), len(xv), _p(yv, _i), len(yv), int(gap),
+                                                ctypes.byref(c), ctypes.byref(e))
+    if rc != 0:
+        raise ValueError(f"oracle pruned forward failed (code {rc})")
+    return c.value, e.value
 
 
 def round_f16(values):

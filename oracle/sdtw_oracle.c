@@ -275,6 +275,69 @@ int sdtw_oracle_forward_f16(const double* x, int64_t n, const double* y, int64_t
     return ORACLE_OK;
 }
 
+/* -------------------------------------------------- early-INF pruning -- */
+
+/*
+ * Section 8 of the paper (future work) proposes pruning: when the two samples
+ * of a cell are "far" apart, the cell is taken not to lie on the path and its
+ * cost is infinite instead of being computed.  Read here for the integer
+ * modes: a cell with |x_i - y_j| > gap costs +inf, and +inf absorbs every
+ * sum.  Eq. 1 is otherwise unchanged (free start, free end); the cost is +inf
+ * when every cell of the last row is, and then no column ends a path (end -1).
+ * gap >= 0.  PRUNED_INF stands for +inf: above every finite sum of at most
+ * n * 2^17 int8 or uint8 local costs.
+ */
+#define PRUNED_INF ((int64_t)1 << 62)
+
+static int64_t pruned_cost_i64(int64_t a, int64_t b, int64_t gap)
+{
+    const int64_t d = a - b;
+    return (d > gap || -d > gap) ? PRUNED_INF : d * d;
+}
+
+static int64_t sat_add(int64_t a, int64_t b)
+{
+    return (a >= PRUNED_INF || b >= PRUNED_INF) ? PRUNED_INF : a + b;
+}
+
+int sdtw_oracle_forward_pruned_i64(const int64_t* x, int64_t n, const int64_t* y, int64_t m, int64_t gap,
+                                   int64_t* cost, int64_t* end)
+{
+    if (!x || !y || !cost || !end || n < 1 || m < 1 || gap < 0) return ORACLE_EINVAL;
+    int64_t* prev = (int64_t*)malloc((size_t)m * sizeof(int64_t));
+    int64_t* cur = (int64_t*)malloc((size_t)m * sizeof(int64_t));
+    if (!prev || !cur) {
+        free(prev);
+        free(cur);
+        return ORACLE_ENOMEM;
+    }
+    for (int64_t j = 0; j < m; ++j) prev[j] = pruned_cost_i64(x[0], y[j], gap);
+    for (int64_t i = 1; i < n; ++i) {
+        cur[0] = sat_add(prev[0], pruned_cost_i64(x[i], y[0], gap));
+        for (int64_t j = 1; j < m; ++j) {
+            int64_t best = prev[j - 1];
+            if (cur[j - 1] < best) best = cur[j - 1];
+            if (prev[j] < best) best = prev[j];
+            cur[j] = sat_add(best, pruned_cost_i64(x[i], y[j], gap));
+        }
+        int64_t* t = prev;
+        prev = cur;
+        cur = t;
+    }
+    int64_t best = prev[0], arg = 0;
+    for (int64_t j = 1; j < m; ++j) {
+        if (prev[j] < best) {
+            best = prev[j];
+            arg = j;
+        }
+    }
+    *cost = best;
+    *end = best >= PRUNED_INF ? -1 : arg;
+    free(prev);
+    free(cur);
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------------- walk-back -- */
 
 /*

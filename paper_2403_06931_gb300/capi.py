@@ -33,7 +33,7 @@ SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
 SDTW_FLAG_ZNORM_QUERIES = 0x8
 
-ABI_VERSION = 3
+ABI_VERSION = 4
 
 
 class sdtw_config(ctypes.Structure):
@@ -47,7 +47,7 @@ class sdtw_config(ctypes.Structure):
         ("seg_width", ctypes.c_int32),
         ("warps_per_query", ctypes.c_int32),
         ("ckpt_stride", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("prune_gap", ctypes.c_int32),
         ("mem_cap_bytes", ctypes.c_size_t),
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),

@@ -174,7 +174,7 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
     if (p.persistent) {
         // 0 CTAs per SM when the query does not fit in shared memory: the call
         // then fails with SDTW_E_UNSUPPORTED before any launch
-        const int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt);
+        const int per_sm = sdtw::fwd_max_ctas_per_sm(c->cfg.dtype, p.W, p.P, p.smem, p.RT, ckpt, c->cfg.prune_gap > 0);
         p.grid = std::max(1, std::min(B, per_sm * c->sm_count));
     } else {
         p.grid = plain_grid(c->cfg.dtype, B);
@@ -294,6 +294,7 @@ sdtw_status run_forward(sdtw_ctx* c, const void* ref, int64_t M, const void* que
     a.status = c->d_status;
     // the context's normalised copy holds max_total_query_len samples
     a.q_limit = (c->cfg.flags & SDTW_FLAG_ZNORM_QUERIES) ? c->cfg.max_total_query_len : 0;
+    a.prune_gap = c->cfg.prune_gap;
     a.queue = nullptr;
     a.order = nullptr;
     cudaError_t e;
@@ -437,7 +438,8 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_ZNORM_QUERIES) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
-    if (cfg->ckpt_stride < 0 || cfg->reserved0 != 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
+    if (cfg->ckpt_stride < 0 || cfg->prune_gap < 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
+    if (cfg->prune_gap > 0 && !int_mode(cfg->dtype)) return SDTW_E_INVALID;  // pruning: integer modes only
     if (cfg->ckpt_stride != 0 && !sdtw::ckpt_stride_supported(cfg->ckpt_stride)) return SDTW_E_UNSUPPORTED;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
     if (int_mode(cfg->dtype) && cfg->max_query_len > kI8MaxN) return SDTW_E_INVALID;
@@ -814,7 +816,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
                 const bool with_bwd = t_gc && sdtw::bwd_width_supported(W) &&
                                       sdtw::bwd_smem_bytes(N, W, RT, KS) <= kMaxSmem;
                 if (t_gc && !with_bwd) continue;  // a plan the backward cannot use
-                const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt);
+                const int per_sm = sdtw::fwd_max_ctas_per_sm(ctx->cfg.dtype, W, P, p.smem, RT, ckpt, ctx->cfg.prune_gap > 0);
                 if (per_sm <= 0) continue;
                 p.grid = p.persistent ? std::max(1, std::min(B, per_sm * ctx->sm_count)) : plain_grid(ctx->cfg.dtype, B);
                 // one untimed run, then the best of two timed runs

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(32) bwd_band_kernel(const BwdArgs a)
     float* gq = grads ? a.grad_queries + start : nullptr;
     int32_t* path = a.path ? a.path + 2 * start : nullptr;
 
-    // the forward's schedule for this query (sdtw_forward.cu)
+    // the forward's schedule for this query (sdtw_fill.cuh)
     const int lag_last = (a.P - 1) * (32 + kChunk) + 31;
     const int nt = (n + RT - 1) / RT;
     const int Pp = max(nt, lag_last + kChunk);

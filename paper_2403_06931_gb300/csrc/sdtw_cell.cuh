@@ -42,7 +42,7 @@ struct Mode<float> {
     using V = float;  // x, y and D
     using Col = int;  // a column of the running bottom-row minimum
     static constexpr bool kPair = false;
-    // FP32 D values are kept relative to a per-thread base (see sdtw_forward.cu)
+    // FP32 D values are kept relative to a per-thread base (see sdtw_fill.cuh)
     static constexpr bool kRebase = true;
     static __device__ __forceinline__ V inf() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ V empty_cost() { return inf(); }  // empty query
@@ -86,6 +86,17 @@ struct ModeInt {
         const int32_t m = __float_as_int(
             min3_f32(__int_as_float(up), __int_as_float(diag), __int_as_float(left)));
         return d * d + m;
+    }
+    // early-INF pruning (paper Section 8): a cell whose samples differ by more
+    // than gap is +inf, and +inf absorbs (d*d + inf stays below 2^31 and is
+    // clamped back to inf)
+    static __device__ __forceinline__ V cell_pruned(V x, V y, V up, V diag, V left, int gap)
+    {
+        const int32_t d = x - y;
+        const int32_t m = __float_as_int(
+            min3_f32(__int_as_float(up), __int_as_float(diag), __int_as_float(left)));
+        const int32_t t = min(d * d + m, inf());
+        return abs(d) > gap ? inf() : t;
     }
 };
 

@@ -33,7 +33,7 @@ constexpr int kIntMaxN = 32896;
 
 // FP32 mode: a strip whose left input at the first row of a tile lies more
 // than this far below the strip's integer base is rebased to that input before
-// the tile (see sdtw_forward.cu).  The backward replays the same decision.
+// the tile (see sdtw_fill.cuh).  The backward replays the same decision.
 constexpr float kRebaseBelow = 256.f;
 
 // Dynamic shared memory one CTA may use on sm_103a.  Shared-memory sizes are
@@ -82,6 +82,7 @@ struct FwdArgs {
     int64_t* ck_end;
     int* status;
     int64_t q_limit;     // > 0: queries end within this many samples (a ragged query past it is flagged)
+    int32_t prune_gap;   // integer modes: > 0 prunes cells whose samples differ by more (Section 8); 0: off
     int* queue;          // persistent mode: device work counter (reset to 0 before the launch)
     const int32_t* order;// persistent mode: query order (longest first), or nullptr
 };
@@ -101,10 +102,13 @@ struct FwdPlan {
 bool fwd_width_supported(sdtw_dtype dt, int W);
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT);
 // 0 when smem exceeds kMaxSmemBytes or the plan cannot be resident
-int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool ckpt);
+int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool ckpt, bool prune = false);
 int64_t fwd_total_steps(int64_t M, int N, int W, int P, int RT);
 cudaError_t launch_forward(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_order_by_length(const int64_t* offsets, int32_t B, int32_t* order, cudaStream_t s);
+// the integer modes (sdtw_forward_int.cu), with or without pruning
+int fwd_max_ctas_per_sm_int(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool prune);
+cudaError_t launch_forward_int(sdtw_dtype dt, const FwdPlan& plan, const FwdArgs& a, cudaStream_t s);
 
 struct BwdArgs {
     const float* ref;
@@ -137,7 +141,7 @@ struct BwdArgs {
     int64_t q_limit; // > 0: queries end within this many samples (a ragged query past it is flagged)
 };
 
-// Checkpoint geometry of a forward plan (sdtw_forward.cu): floats of one
+// Checkpoint geometry of a forward plan (sdtw_forward.cu, sdtw_fill.cuh): floats of one
 // thread's record, wavefront checkpoints (one every KS steps) of the schedule
 // for a query of n rows, and the per-query slot sizes of the two checkpoint
 // arrays.  Checkpoint strides are 16, 32 or 64 steps; the checkpointing fill

@@ -162,3 +162,12 @@ def test_checkpoint_strides_accepted_by_create(lib):
         cfg.ckpt_stride = ks
         cfg.flags = capi.SDTW_FLAG_GRAD
         assert capi.sdtw_create(cfg)[0] == want, ks
+
+
+def test_prune_gap_accepted_only_for_integer_modes(lib):
+    for dtype, gap, want in ((capi.SDTW_F32, 5, capi.SDTW_E_INVALID), (capi.SDTW_F16, 5, capi.SDTW_E_INVALID),
+                             (capi.SDTW_I8, -1, capi.SDTW_E_INVALID), (capi.SDTW_U8, -3, capi.SDTW_E_INVALID)):
+        cfg = capi.sdtw_config_init()
+        cfg.dtype = dtype
+        cfg.prune_gap = gap
+        assert capi.sdtw_create(cfg)[0] == want, (dtype, gap)

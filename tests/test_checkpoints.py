@@ -1,6 +1,6 @@
 """CPU model of the backward checkpoints and of the backward's band replay.
 
-The checkpointing forward (csrc/sdtw_forward.cu) stores, every KS steps
+The checkpointing forward (csrc/sdtw_fill.cuh) stores, every KS steps
 (KS = 16, 32 or 64), the state of its wavefront: each thread's latest row (its
 strip of W columns, relative to the thread's integer base), the right-hand
 cells of its tile's other rows, its diagonal input and its base, as they stand

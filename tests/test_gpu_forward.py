@@ -97,6 +97,30 @@ def test_stretched_paths_fp32(gpu, W, scale):
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
 
 
+@pytest.mark.parametrize("dtype", ["f32", "i8", "f16"])
+def test_unaligned_reference_matches_aligned(gpu, dtype):
+    # strips are loaded as vectors of four samples only when the reference is
+    # aligned for them; a reference that starts one sample into a buffer takes
+    # the per-sample loads and must give the same results
+    w = inputs.tiny(B=4, N=120, M=5003, seed=83)
+    tdt = {"f32": torch.float32, "i8": torch.int8, "f16": torch.float16}[dtype]
+    if dtype == "i8":
+        ref_h, q_h = inputs.quantize_i8(w.ref), inputs.quantize_i8(w.queries)
+    else:
+        ref_h, q_h = w.ref, w.queries
+    buf = torch.zeros(w.M + 1, dtype=tdt, device=gpu)
+    buf[1:] = torch.from_numpy(np.ascontiguousarray(ref_h)).to(gpu).to(tdt)
+    unaligned = buf[1:]
+    aligned = unaligned.clone()
+    q = torch.from_numpy(np.ascontiguousarray(q_h)).to(gpu).to(tdt)
+    ctx = SdtwContext(dtype=dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=w.N)
+    c0, e0 = ctx.forward(aligned, q)
+    c1, e1 = ctx.forward(unaligned, q)
+    assert ctx.device_status() == capi.SDTW_OK
+    assert torch.equal(c0, c1) and torch.equal(e0, e1)
+    ctx.close()
+
+
 def test_exact_cut_has_zero_cost(gpu):
     w = inputs.tiny(B=1, N=10, M=3000, seed=5)
     y = w.ref

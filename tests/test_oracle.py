@@ -609,3 +609,63 @@ def test_f16_dp_close_to_f64_on_paper_shaped_inputs(oracle_mod):
         assert abs(c16 - c64) <= 64 * 2.0 ** -11 * max(c64, 1.0) * 2
     with pytest.raises(ValueError):
         oracle_mod.forward_f16(np.array([0.1]), np.array([0.2]))        # not binary16 values
+
+
+# ---------------------------------------------------------------------------
+# Early-INF pruning (Section 8): a cell whose samples differ by more than the
+# gap costs +inf.  Pinned by brute force over whole paths (a path through a
+# pruned cell costs +inf), the gap that prunes nothing, and monotonicity.
+
+def brute_force_pruned(x, y, gap):
+    """Minimum over whole warp paths of the path cost, +inf for a path that
+    crosses a cell whose samples differ by more than gap (no recurrence)."""
+    n, m = len(x), len(y)
+    best = [math.inf] * m
+
+    def extend(i, j, acc):
+        if abs(x[i] - y[j]) > gap:
+            return                                   # this path costs +inf
+        acc = acc + (x[i] - y[j]) ** 2
+        if i == n - 1 and acc < best[j]:
+            best[j] = acc
+        if i + 1 < n:
+            extend(i + 1, j, acc)
+        if j + 1 < m:
+            extend(i, j + 1, acc)
+        if i + 1 < n and j + 1 < m:
+            extend(i + 1, j + 1, acc)
+
+    for s in range(m):
+        extend(0, s, 0)
+    return best
+
+
+@pytest.mark.parametrize("n,m", [(1, 4), (3, 3), (4, 5), (5, 4), (6, 6), (2, 7), (7, 2)])
+def test_pruned_dp_equals_brute_force(oracle_mod, n, m):
+    rng = np.random.default_rng(55 + 10 * n + m)
+    for gap in (0, 1, 2, 3, 5, 100):
+        for _ in range(3):
+            x = [int(v) for v in rng.integers(-4, 5, size=n)]
+            y = [int(v) for v in rng.integers(-4, 5, size=m)]
+            bf = brute_force_pruned(x, y, gap)
+            c, e = oracle_mod.forward_pruned(np.array(x), np.array(y), gap)
+            if math.isinf(min(bf)):
+                assert c == oracle_mod.PRUNED_INF and e == -1
+            else:
+                assert c == min(bf) and e == bf.index(min(bf))
+
+
+def test_pruning_that_prunes_nothing_is_the_plain_dp(oracle_mod):
+    w = inputs.paper_i8(B=3, N=60, M=700, seed=56)
+    for q in range(w.B):
+        x, y = w.query(q).astype(np.int64), w.ref.astype(np.int64)
+        gap = int(np.abs(x[:, None] - y[None, :]).max())
+        assert oracle_mod.forward_pruned(x, y, gap) == oracle_mod.forward(x, y)
+
+
+def test_pruned_cost_never_falls_as_the_gap_shrinks(oracle_mod):
+    w = inputs.paper_i8(B=2, N=80, M=900, seed=57)
+    for q in range(w.B):
+        x, y = w.query(q).astype(np.int64), w.ref.astype(np.int64)
+        costs = [oracle_mod.forward_pruned(x, y, g)[0] for g in (200, 40, 20, 10, 5, 2, 0)]
+        assert all(a <= b for a, b in zip(costs, costs[1:]))

@@ -1,6 +1,6 @@
 """CPU model of the forward kernel's schedule (paper Section 5.2 wavefront).
 
-The CUDA forward (csrc/sdtw_forward.cu) runs a chain of 32*P threads, each
+The CUDA forward (csrc/sdtw_fill.cuh) runs a chain of 32*P threads, each
 owning W reference columns and advancing two query rows per step (a 2 x W
 tile); thread l lags thread l-1 by one step inside a warp, warp w lags warp
 w-1 by 32 + kChunk steps, tile edges cross warps through a ring of kRing

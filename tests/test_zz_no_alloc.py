@@ -73,6 +73,34 @@ def test_noalloc_int8_matches_forward_twice(gpu):
         assert torch.equal(cost.cpu(), c_ref.cpu()) and torch.equal(end.cpu(), e_ref.cpu())
 
 
+@pytest.mark.parametrize("dtype", ["f16", "u8"])
+def test_noalloc_binary16_and_codebook_codes_match_forward_twice(gpu, dtype):
+    w = inputs.tiny(B=9, N=150, M=12000, seed=615)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    if dtype == "f16":
+        ref, qs = ref.half(), qs.half()
+        lib_dt, cdt = capi.SDTW_F16, torch.float32
+    else:
+        from paper_2403_06931_gb300.sdtw import codebook_encode, codebook_fit
+        params = codebook_fit(ref)
+        ref, qs = codebook_encode(ref, params), codebook_encode(qs, params)
+        lib_dt, cdt = capi.SDTW_U8, torch.int32
+    ctx = SdtwContext(dtype=dtype, max_ref_len=w.M, max_batch=w.B, max_query_len=w.N)
+    c_ref, e_ref = ctx.forward(ref, qs)
+    torch.cuda.synchronize()
+    ctx.close()
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        cost = torch.full((w.B,), -1, dtype=cdt, device=gpu)
+        end = torch.full((w.B,), -7, dtype=torch.int64, device=gpu)
+        st = capi.sdtw_forward_noalloc(lib_dt, ref.data_ptr(), w.M, qs.data_ptr(), None, w.B, w.N,
+                                       cost.data_ptr(), end.data_ptr(), s)
+        assert st == capi.SDTW_OK
+        torch.cuda.synchronize()
+        assert torch.equal(cost, c_ref) and torch.equal(end, e_ref)
+
+
 def test_noalloc_over_long_query_gets_the_empty_outputs(gpu):
     # a ragged query longer than N cannot be reported (no context): it gets the
     # empty query's outputs, and the others are computed as by sdtw_forward
