@@ -150,13 +150,14 @@ sdtw_status ensure(sdtw_ctx* c, DevBuf& b, size_t bytes)
 // default plan for a forward call
 FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged, bool ckpt)
 {
-    // defaults measured on the paper's batch: 4 rows per thread, four warps
-    // per query, and 24 columns per thread for the plain fill, 32 with
-    // checkpoints (the backward's wider windows give fewer band changes)
+    // defaults measured on the paper's batch: four warps per query; the plain
+    // FP32 fill with 8-row tiles of 24 columns, every other fill with 4-row
+    // tiles, of 24 columns, or 32 with checkpoints (the backward's wider
+    // windows give fewer band changes)
     FwdPlan p;
     p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : 24);
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
-    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 4;
+    p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : (sdtw::fwd_plan_supported(c->cfg.dtype, p.W, 8, ckpt) ? 8 : 4);
     p.KS = c->cfg.ckpt_stride > 0 ? c->cfg.ckpt_stride : kDefaultStride;
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
@@ -437,7 +438,12 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_KEEP_CHECKPOINTS) && !(cfg->flags & SDTW_FLAG_GRAD)) return SDTW_E_INVALID;
     if ((cfg->flags & SDTW_FLAG_ZNORM_QUERIES) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
-    if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4) return SDTW_E_INVALID;
+    if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4 && cfg->tile_rows != 8) return SDTW_E_INVALID;
+    // 8-row tiles: the plain FP32 fill only (no checkpoints), 16 to 28 columns
+    if (cfg->tile_rows == 8 &&
+        (cfg->dtype != SDTW_F32 || (cfg->flags & SDTW_FLAG_GRAD) ||
+         (cfg->seg_width > 0 && !sdtw::fwd_plan_supported(SDTW_F32, cfg->seg_width, 8, false))))
+        return SDTW_E_INVALID;
     if (cfg->ckpt_stride < 0 || cfg->prune_gap < 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
     if (cfg->prune_gap > 0 && !int_mode(cfg->dtype)) return SDTW_E_INVALID;  // pruning: integer modes only
     if (cfg->ckpt_stride != 0 && !sdtw::ckpt_stride_supported(cfg->ckpt_stride)) return SDTW_E_UNSUPPORTED;
@@ -789,7 +795,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
     int best_w = 0, best_p = 0, best_rt = 0, best_ks = 0;
     const int Ws[] = {8, 16, 20, 24, 28, 32};
     const int Ps[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
-    const int RTs[] = {2, 4};
+    const int RTs[] = {2, 4, 8};
     // the checkpoint stride is an axis only when checkpoints are stored (and
     // the caller did not fix it); a stride whose checkpoints do not fit the
     // arena under the memory cap is skipped like any other plan
@@ -802,6 +808,7 @@ sdtw_status sdtw_autotune(sdtw_ctx* ctx, const void* ref, int64_t M, const void*
         for (int W : Ws) {
             for (int P : Ps) {
                 if (static_cast<int64_t>(32) * P * W > 4 * M && P > 1) continue;
+                if (!sdtw::fwd_plan_supported(ctx->cfg.dtype, W, RT, ckpt)) continue;
                 FwdPlan p = default_fwd_plan(ctx, B, N, M, ragged, ckpt);
                 p.W = W;
                 p.P = P;

@@ -142,6 +142,21 @@ __device__ __forceinline__ void load_strip(const Tin* ref, int base, int M, bool
 template <int RT, typename V>
 __device__ __forceinline__ void load_x(const V* xs, int p, V (&x)[RT])
 {
+    if constexpr (RT == 8) {
+        // eight FP32 samples: two 16-byte loads
+        static_assert(std::is_same<V, float>::value, "8-row tiles are FP32 only");
+        const float4* p4 = reinterpret_cast<const float4*>(xs) + 2 * p;
+        const float4 u = p4[0], w = p4[1];
+        x[0] = u.x;
+        x[1] = u.y;
+        x[2] = u.z;
+        x[3] = u.w;
+        x[4] = w.x;
+        x[5] = w.y;
+        x[6] = w.z;
+        x[7] = w.w;
+        return;
+    } else {
     const auto v = reinterpret_cast<const typename VecOf<V, RT>::T*>(xs)[p];
     if constexpr (std::is_same<V, __half2>::value) {
         x[0] = Mode<__half>::from_bits(v.x);
@@ -157,6 +172,7 @@ __device__ __forceinline__ void load_x(const V* xs, int p, V (&x)[RT])
             x[2] = v.z;
             x[3] = v.w;
         }
+    }
     }
 }
 
@@ -324,22 +340,24 @@ __device__ __forceinline__ void store_rows(float* dst, const float (&v)[RT])
 // Register cap per segment width and tile height: the strip's samples and
 // previous row (2W), the tile's short-lived values and bookkeeping, leaving
 // room for several CTAs per SM.
-// (one template argument, W * 8 + RT, as the attribute takes a single expression)
+// (one template argument, W * 16 + RT, as the attribute takes a single expression)
 template <int WRT>
 constexpr int fwd_reg_cap()
 {
-    constexpr int W = WRT / 8, RT = WRT % 8;
+    constexpr int W = WRT / 16, RT = WRT % 16;
+    if (RT == 8) return W <= 16 ? 112 : W <= 20 ? 120 : 128;
     return W <= 8 ? (RT == 2 ? 72 : 80) : W <= 16 ? (RT == 2 ? 88 : 96) : W <= 20 ? (RT == 2 ? 104 : 112) : W <= 24 ? (RT == 2 ? 112 : 120) : 128;
 }
 
 template <typename Tin, int W, int RT, bool CKPT, bool PRUNE>
-__global__ void __maxnreg__(fwd_reg_cap<W * 8 + RT>())
+__global__ void __maxnreg__(fwd_reg_cap<W * 16 + RT>())
 fwd_chain_kernel(const FwdArgs a)
 {
     using Md = Mode<Tin>;
     using V = typename Md::V;
     using E = Edge<V, RT>;
-    static_assert(RT == 2 || RT == 4, "tiles of 2 or 4 rows");
+    static_assert(RT == 2 || RT == 4 || RT == 8, "tiles of 2, 4 or 8 rows");
+    static_assert(RT != 8 || !CKPT, "8-row tiles have no checkpoints");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_query;

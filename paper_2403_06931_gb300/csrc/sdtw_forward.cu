@@ -58,6 +58,18 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
     case 32: return f(Inst<Tin, 32, RTv, CK>{});                          \
     default: return cudaErrorInvalidValue;                                \
     }
+    if (RT == 8) {
+        // 8-row tiles: the plain FP32 fill (the per-step work of shuffles,
+        // conversions and loop control spread over 8 rows), W up to 28
+        if (dt != SDTW_F32 || ckpt) return cudaErrorInvalidValue;
+        switch (W) {
+        case 16: return f(Inst<float, 16, 8, false>{});
+        case 20: return f(Inst<float, 20, 8, false>{});
+        case 24: return f(Inst<float, 24, 8, false>{});
+        case 28: return f(Inst<float, 28, 8, false>{});
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (RT != 2 && RT != 4) return cudaErrorInvalidValue;
     if (dt == SDTW_F16) {
         if (ckpt) return cudaErrorInvalidValue;
@@ -75,15 +87,22 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
 
 bool fwd_width_supported(sdtw_dtype, int W) { return W == 8 || W == 16 || W == 20 || W == 24 || W == 28 || W == 32; }
 
+bool fwd_plan_supported(sdtw_dtype dt, int W, int RT, bool ckpt)
+{
+    if (!fwd_width_supported(dt, W)) return false;
+    if (RT == 2 || RT == 4) return true;
+    return RT == 8 && dt == SDTW_F32 && !ckpt && W >= 16 && W <= 28;
+}
+
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT)
 {
     // ring [P][kRing] and column buffer [Npad/RT] of edges (16 bytes for RT = 2,
-    // 32 for RT = 4), query samples [Npad] and the reduction (value, index)[P],
+    // 32 for RT = 4, 48 for RT = 8), query samples [Npad] and the reduction (value, index)[P],
     // 4-byte elements; 64-bit, so that no query length wraps to a small size
     (void)W;
     if (N < 0) N = 0;
     const int64_t npad = (N + RT - 1) / RT * RT;
-    const int64_t esz = RT == 2 ? 16 : 32;
+    const int64_t esz = RT == 2 ? 16 : RT == 4 ? 32 : 48;
     const int64_t red = dt == SDTW_F16 ? 4 : 2;  // binary16 pairs reduce two (value, column) pairs per warp
     return esz * (static_cast<int64_t>(P) * kRing + npad / RT) + 4 * (npad + red * static_cast<int64_t>(P));
 }

@@ -90,7 +90,7 @@ struct FwdArgs {
 struct FwdPlan {
     int W = 16;          // segment width: reference columns per thread
     int P = 8;           // warps per query chain
-    int RT = 2;          // query rows per thread per step (tile height)
+    int RT = 2;          // query rows per thread per step (tile height: 2, 4, or 8 for the plain FP32 fill)
     int KS = kChunk;     // with checkpoints: steps between wavefront checkpoints (16, 32 or 64)
     bool persistent = false;
     int grid = 0;
@@ -100,6 +100,9 @@ struct FwdPlan {
 
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
+// a (W, RT) the fill has an instantiation for: RT 2 or 4 for every mode, RT 8
+// for the plain FP32 fill at W 16..28
+bool fwd_plan_supported(sdtw_dtype dt, int W, int RT, bool ckpt);
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT);
 // 0 when smem exceeds kMaxSmemBytes or the plan cannot be resident
 int fwd_max_ctas_per_sm(sdtw_dtype dt, int W, int P, int64_t smem, int RT, bool ckpt, bool prune = false);

@@ -52,10 +52,12 @@ def test_shapes_fp32(gpu, B, N, M):
     assert parity.check_forward_f32(w.ref, w.query, range(B), cost, end) == []
 
 
-@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("RT", [2, 4, 8])
 @pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
 @pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 8, 16])
 def test_every_plan_fp32(gpu, W, P, RT):
+    if RT == 8 and not 16 <= W <= 28:
+        pytest.skip("8-row tiles are built for 16 to 28 columns")
     w = inputs.tiny(B=3, N=91, M=6000, seed=77)
     cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
     assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
@@ -71,15 +73,19 @@ def test_every_plan_i8_bit_exact(gpu, W, P, RT):
     assert parity.check_forward_i8(w.ref, w.query, range(w.B), cost, end) == []
 
 
-@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("RT", [2, 4, 8])
 @pytest.mark.parametrize("W", [8, 16, 28, 32])
 @pytest.mark.parametrize("P", [1, 2, 4])
 def test_fast_path_plans(gpu, W, P, RT):
-    # queries long enough that most chunks take the fast path; lengths of every residue mod 4
-    for N in (1501, 1202, 1403, 1200):
+    # queries long enough that most chunks take the fast path; lengths of every residue mod 8
+    if RT == 8 and not 16 <= W <= 28:
+        pytest.skip("8-row tiles are built for 16 to 28 columns")
+    for N in (1501, 1202, 1403, 1200, 1605, 1206, 1207):
         w = inputs.tiny(B=2, N=N, M=20000, seed=79 + N)
         cost, end = run_fwd(gpu, w.ref, w.queries, seg_width=W, warps_per_query=P, tile_rows=RT)
         assert parity.check_forward_f32(w.ref, w.query, range(w.B), cost, end) == []
+        if RT == 8:
+            continue    # the integer modes have 2- and 4-row tiles
         wi = inputs.paper_i8(B=2, N=N, M=20000, seed=80 + N)
         cost, end = run_fwd(gpu, wi.ref, wi.queries, dtype="i8", seg_width=W, warps_per_query=P, tile_rows=RT)
         assert parity.check_forward_i8(wi.ref, wi.query, range(wi.B), cost, end) == []
@@ -161,6 +167,18 @@ def test_ragged_with_empty_and_single_queries(gpu):
     for q in range(len(lengths)):
         if lengths[q] == 0:
             assert np.isinf(cost[q]) and cost[q] > 0 and end[q] == -1
+
+
+@pytest.mark.parametrize("RT", [4, 8])
+def test_ragged_every_residue(gpu, RT):
+    # ragged lengths of every residue modulo the tile height, in one persistent launch
+    rng = np.random.default_rng(14)
+    lengths = np.array([1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 255, 256, 257, 700, 703], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    ref = inputs.znorm(np.cumsum(rng.standard_normal(9000))).astype(np.float32)
+    flat = rng.standard_normal(int(offs[-1])).astype(np.float32)
+    cost, end = run_fwd(gpu, ref, flat, offsets=offs, N=703, seg_width=24, tile_rows=RT)
+    assert parity.check_forward_f32(ref, lambda q: flat[offs[q]:offs[q + 1]], range(len(lengths)), cost, end) == []
 
 
 def test_ragged_i8(gpu):
