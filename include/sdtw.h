@@ -105,8 +105,8 @@ typedef struct sdtw_config {
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
     uint64_t spin_limit;         /* reserved: no kernel of this build waits on a flag; must be 0 */
     uint32_t flags;              /* SDTW_FLAG_* */
-    int32_t tile_rows;           /* query rows a thread advances per step: 2 or 4, or 8 for the plain FP32 fill
-                                    (SDTW_F32 without SDTW_FLAG_GRAD, seg_width 16 to 28); 0 = chosen by the
+    int32_t tile_rows;           /* query rows a thread advances per step: 2 or 4, or 8 for the plain fills
+                                    (any dtype without SDTW_FLAG_GRAD, seg_width 16 to 28); 0 = chosen by the
                                     library */
 } sdtw_config;
 
@@ -142,8 +142,8 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * SDTW_FLAG_GRAD is set), sized from the cfg maxima and allocated here.
  * *out receives the context, or NULL on error.
  * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
- * SDTW_FLAG_GRAD with SDTW_I8, an unsupported seg_width or tile_rows (8 outside
- * the plain FP32 fill), a
+ * SDTW_FLAG_GRAD with a dtype other than SDTW_F32, an unsupported seg_width or
+ * tile_rows (8 with SDTW_FLAG_GRAD or a seg_width outside 16 to 28), a
  * non-zero spin_limit, a negative ckpt_stride or prune_gap, a prune_gap with
  * SDTW_F32 or SDTW_F16),
  * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 16, 32 or 64, or a

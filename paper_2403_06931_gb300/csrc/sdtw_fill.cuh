@@ -143,18 +143,13 @@ template <int RT, typename V>
 __device__ __forceinline__ void load_x(const V* xs, int p, V (&x)[RT])
 {
     if constexpr (RT == 8) {
-        // eight FP32 samples: two 16-byte loads
-        static_assert(std::is_same<V, float>::value, "8-row tiles are FP32 only");
-        const float4* p4 = reinterpret_cast<const float4*>(xs) + 2 * p;
-        const float4 u = p4[0], w = p4[1];
-        x[0] = u.x;
-        x[1] = u.y;
-        x[2] = u.z;
-        x[3] = u.w;
-        x[4] = w.x;
-        x[5] = w.y;
-        x[6] = w.z;
-        x[7] = w.w;
+        // eight 4-byte samples (float, int32 or a binary16 pair): two 16-byte loads
+        static_assert(sizeof(V) == 4, "4-byte samples");
+        const uint4* p4 = reinterpret_cast<const uint4*>(xs) + 2 * p;
+        const uint4 u = p4[0], w = p4[1];
+        const uint32_t b[8] = {u.x, u.y, u.z, u.w, w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int r = 0; r < 8; ++r) memcpy(&x[r], &b[r], 4);
         return;
     } else {
     const auto v = reinterpret_cast<const typename VecOf<V, RT>::T*>(xs)[p];

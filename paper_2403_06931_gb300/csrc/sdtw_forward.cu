@@ -58,17 +58,21 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
     case 32: return f(Inst<Tin, 32, RTv, CK>{});                          \
     default: return cudaErrorInvalidValue;                                \
     }
+#define SDTW_W8(Tin)                                                      \
+    switch (W) {                                                          \
+    case 16: return f(Inst<Tin, 16, 8, false>{});                         \
+    case 20: return f(Inst<Tin, 20, 8, false>{});                         \
+    case 24: return f(Inst<Tin, 24, 8, false>{});                         \
+    case 28: return f(Inst<Tin, 28, 8, false>{});                         \
+    default: return cudaErrorInvalidValue;                                \
+    }
     if (RT == 8) {
-        // 8-row tiles: the plain FP32 fill (the per-step work of shuffles,
+        // 8-row tiles: plain fills only (the per-step work of shuffles,
         // conversions and loop control spread over 8 rows), W up to 28
-        if (dt != SDTW_F32 || ckpt) return cudaErrorInvalidValue;
-        switch (W) {
-        case 16: return f(Inst<float, 16, 8, false>{});
-        case 20: return f(Inst<float, 20, 8, false>{});
-        case 24: return f(Inst<float, 24, 8, false>{});
-        case 28: return f(Inst<float, 28, 8, false>{});
-        default: return cudaErrorInvalidValue;
-        }
+        if (ckpt) return cudaErrorInvalidValue;
+        if (dt == SDTW_F16) { SDTW_W8(__half) }
+        if (dt == SDTW_F32) { SDTW_W8(float) }
+        return cudaErrorInvalidValue;
     }
     if (RT != 2 && RT != 4) return cudaErrorInvalidValue;
     if (dt == SDTW_F16) {
@@ -80,6 +84,7 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
         if (RT == 2) { SDTW_W(float, 2, true) } else { SDTW_W(float, 4, true) }
     }
     if (RT == 2) { SDTW_W(float, 2, false) } else { SDTW_W(float, 4, false) }
+#undef SDTW_W8
 #undef SDTW_W
 }
 
@@ -91,7 +96,7 @@ bool fwd_plan_supported(sdtw_dtype dt, int W, int RT, bool ckpt)
 {
     if (!fwd_width_supported(dt, W)) return false;
     if (RT == 2 || RT == 4) return true;
-    return RT == 8 && dt == SDTW_F32 && !ckpt && W >= 16 && W <= 28;
+    return RT == 8 && !ckpt && W >= 16 && W <= 28;
 }
 
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT)

@@ -24,9 +24,17 @@ cudaError_t dispatch_int(sdtw_dtype dt, int W, int RT, bool prune, F&& f)
     case 32: return f(Inst<Tin, 32, RTv, false, PR>{});                   \
     default: return cudaErrorInvalidValue;                                \
     }
+#define SDTW_W8(Tin, PR)                                                  \
+    switch (W) {                                                          \
+    case 16: return f(Inst<Tin, 16, 8, false, PR>{});                     \
+    case 20: return f(Inst<Tin, 20, 8, false, PR>{});                     \
+    case 24: return f(Inst<Tin, 24, 8, false, PR>{});                     \
+    case 28: return f(Inst<Tin, 28, 8, false, PR>{});                     \
+    default: return cudaErrorInvalidValue;                                \
+    }
 #define SDTW_RT(Tin, PR)                                                  \
-    if (RT == 2) { SDTW_W(Tin, 2, PR) } else { SDTW_W(Tin, 4, PR) }
-    if (RT != 2 && RT != 4) return cudaErrorInvalidValue;
+    if (RT == 2) { SDTW_W(Tin, 2, PR) } else if (RT == 4) { SDTW_W(Tin, 4, PR) } else { SDTW_W8(Tin, PR) }
+    if (RT != 2 && RT != 4 && RT != 8) return cudaErrorInvalidValue;
     if (dt == SDTW_I8) {
         if (prune) { SDTW_RT(int8_t, true) } else { SDTW_RT(int8_t, false) }
     }
@@ -35,6 +43,7 @@ cudaError_t dispatch_int(sdtw_dtype dt, int W, int RT, bool prune, F&& f)
     }
     return cudaErrorInvalidValue;
 #undef SDTW_RT
+#undef SDTW_W8
 #undef SDTW_W
 }
 
