@@ -42,11 +42,12 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM traffic of one checkpointing forward launch on the paper batch, valid
 # only while the forward kernel's code hashes to FWD_SRC_SHA (else reported as
 # null).  Captured on 128 of the 512 queries with the default plan (32 columns x
-# 4 rows per thread; 2,072,064 bytes read + 1,362,158,080 written: the writes
-# are the per-query checkpoints) and scaled by 4 to the 512-query launch;
-# profiles/fwd_chain_kernel_f32_ckpt_W32_RT4_paper_512x2000_vs_100000.md
-FWD_SRC_SHA = "2e1ac1a31cedb5f3"
-FWD_TRAFFIC_BYTES = 4 * (2_072_064 + 1_362_158_080)
+# 4 rows per thread, a checkpoint every 16 steps; 2,444,288 bytes read +
+# 2,387,886,848 written: the writes are the per-query checkpoints) and scaled by
+# 4 to the 512-query launch;
+# profiles/fwd_chain_kernel_f32_ckpt_W32_RT4_KS16_paper_512x2000_vs_100000.md
+FWD_SRC_SHA = "f2eb11686c846bca"
+FWD_TRAFFIC_BYTES = 4 * (2_444_288 + 2_387_886_848)
 
 
 def src_sha(*paths):

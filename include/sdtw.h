@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SDTW_ABI_VERSION 4
+#define SDTW_ABI_VERSION 5
 
 typedef struct sdtw_ctx sdtw_ctx;
 
@@ -56,7 +56,8 @@ typedef enum sdtw_status {
     SDTW_E_INVALID = 1,     /* bad argument (null pointer, N<1, M<1, B<0, dtype mismatch, size over a configured maximum) */
     SDTW_E_NOMEM = 2,       /* device or host workspace could not be allocated, or would exceed mem_cap_bytes */
     SDTW_E_CUDA = 3,        /* a CUDA runtime call failed; the CUDA error text is kept in the context */
-    SDTW_E_TIMEOUT = 4,     /* reserved for a bounded device-side wait that ran out; no kernel of this build waits */
+    SDTW_E_TIMEOUT = 4,     /* a bounded device-side wait ran out (the backward's walker and helpers wait on one
+                               another in shared memory for at most 2 s each) */
     SDTW_E_UNSUPPORTED = 5  /* a valid request this build does not implement (e.g. backward in int8 mode) */
 } sdtw_status;
 
@@ -103,11 +104,17 @@ typedef struct sdtw_config {
                                     than prune_gap costs +inf, and +inf absorbs every sum; a query with no path
                                     left gets cost INT32_MAX and end -1 */
     size_t mem_cap_bytes;        /* cap on device workspace; 0 = 16 GiB */
-    uint64_t spin_limit;         /* reserved: no kernel of this build waits on a flag; must be 0 */
+    uint64_t spin_limit;         /* reserved, must be 0 (the backward's helpers wait on flags in shared memory with
+                                    a fixed limit of 2 s each) */
     uint32_t flags;              /* SDTW_FLAG_* */
     int32_t tile_rows;           /* query rows a thread advances per step: 2 or 4, or 8 for the plain fills
                                     (any dtype without SDTW_FLAG_GRAD, seg_width 16 to 28); 0 = chosen by the
                                     library */
+    int32_t bwd_warps;           /* warps per query in sdtw_backward and sdtw_path: 1 = one warp walks the path
+                                    and recomputes every band; 2 to 4 = that warp and 1 to 3 helpers that
+                                    recompute the bands a path staying on its current row would visit next;
+                                    0 = chosen by the library (3, fewer if the CTA's shared memory would not
+                                    fit); the results are the same for every value */
 } sdtw_config;
 
 /* Description of how a call of a given shape will run (for reports and tests). */
@@ -124,6 +131,7 @@ typedef struct sdtw_plan {
     int64_t sweep_cols;      /* reference columns covered by one sweep of the chain */
     int32_t tile_rows;       /* query rows a thread advances per step */
     int32_t ckpt_cols;       /* K = 8 * seg_width: columns between boundary-column checkpoints (0 when none) */
+    int32_t bwd_warps;       /* warps per query of the backward (0 when the plan has no backward) */
 } sdtw_plan;
 
 /* ABI version this library was built with (SDTW_ABI_VERSION). */
@@ -145,7 +153,7 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * SDTW_FLAG_GRAD with a dtype other than SDTW_F32, an unsupported seg_width or
  * tile_rows (8 with SDTW_FLAG_GRAD or a seg_width outside 16 to 28), a
  * non-zero spin_limit, a negative ckpt_stride or prune_gap, a prune_gap with
- * SDTW_F32 or SDTW_F16),
+ * SDTW_F32 or SDTW_F16, a bwd_warps outside 0 to 4),
  * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 16, 32 or 64, or a
  * max_query_len no forward plan can stage in shared memory),
  * SDTW_E_NOMEM (workspace above mem_cap_bytes, too small for one query's

@@ -33,7 +33,7 @@ SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
 SDTW_FLAG_ZNORM_QUERIES = 0x8
 
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 
 class sdtw_config(ctypes.Structure):
@@ -52,6 +52,7 @@ class sdtw_config(ctypes.Structure):
         ("spin_limit", ctypes.c_uint64),
         ("flags", ctypes.c_uint32),
         ("tile_rows", ctypes.c_int32),
+        ("bwd_warps", ctypes.c_int32),
     ]
 
 
@@ -69,6 +70,7 @@ class sdtw_plan(ctypes.Structure):
         ("sweep_cols", ctypes.c_int64),
         ("tile_rows", ctypes.c_int32),
         ("ckpt_cols", ctypes.c_int32),
+        ("bwd_warps", ctypes.c_int32),
     ]
 
     def as_dict(self):

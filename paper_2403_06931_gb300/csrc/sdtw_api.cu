@@ -447,6 +447,7 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
          (cfg->seg_width > 0 && !sdtw::fwd_plan_supported(cfg->dtype, cfg->seg_width, 8, false))))
         return SDTW_E_INVALID;
     if (cfg->ckpt_stride < 0 || cfg->prune_gap < 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
+    if (cfg->bwd_warps < 0 || cfg->bwd_warps > 4) return SDTW_E_INVALID;
     if (cfg->prune_gap > 0 && !int_mode(cfg->dtype)) return SDTW_E_INVALID;  // pruning: integer modes only
     if (cfg->ckpt_stride != 0 && !sdtw::ckpt_stride_supported(cfg->ckpt_stride)) return SDTW_E_UNSUPPORTED;
     if (cfg->warps_per_query < 0 || cfg->warps_per_query > sdtw::kMaxWarpsPerQuery) return SDTW_E_INVALID;
@@ -564,6 +565,7 @@ cudaError_t launch_bwd(sdtw_ctx* ctx, const FwdPlan& p, const CkPtrs& ck, const 
     a.RT = p.RT;
     a.KS = p.KS;
     a.rebase_period = sdtw::ckpt_rebase_period(p.KS);
+    a.warps = ctx->cfg.bwd_warps;
     a.gyq = ck.gyq;
     a.span = ck.span;
     a.status = ctx->d_status;
@@ -903,6 +905,7 @@ sdtw_status sdtw_get_plan(sdtw_ctx* ctx, int32_t B, int32_t N, int64_t M, int32_
                       : 0;
     plan->sweep_cols = static_cast<int64_t>(32) * p.P * p.W;
     plan->tile_rows = p.RT;
+    plan->bwd_warps = backward ? sdtw::bwd_warps(N, p.W, p.RT, p.KS, ctx->cfg.bwd_warps) : 0;
     return SDTW_OK;
 }
 

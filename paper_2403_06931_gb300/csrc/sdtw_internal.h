@@ -138,6 +138,7 @@ struct BwdArgs {
     int32_t W, P, RT;
     int32_t KS;             // steps between the forward's wavefront checkpoints: a band's height in steps
     int32_t rebase_period;  // the forward's steps between rebases
+    int32_t warps;          // warps per query: 1 = the walker alone, 2..4 with helpers, 0 = the library's choice
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
     int64_t* span;   // [B][2] first and last column of each query's path
     int* status;
@@ -160,7 +161,13 @@ int64_t ck_slot_floats(int64_t M, int N, int K);
 
 // Backward launches (sdtw_backward.cu).
 bool bwd_width_supported(int W);
-int64_t bwd_smem_bytes(int64_t N, int W, int RT, int KS);
+// Shared memory of a backward CTA with `warps` warps (one band slot each), and
+// the warps a launch uses: `requested` (1 = the walker alone, up to 4), or the
+// library's choice for 0, reduced until the CTA fits; 0 if none fits or the
+// request is out of range.
+int64_t bwd_smem_bytes(int64_t N, int W, int RT, int KS, int warps = 1);
+int bwd_warps(int64_t N, int W, int RT, int KS, int requested);
+int bwd_dir_rows(int RT, int KS);
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_grad_ref_reduce(const float* gyq, const int64_t* span, int32_t B, int64_t M,
                                    bool accumulate, float* grad_ref, cudaStream_t s);

@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--ckpt-stride", type=int, default=0, help="steps between wavefront checkpoints (16, 32, 64)")
+    ap.add_argument("--bwd-warps", type=int, default=0,
+                    help="warps per query in the backward (1 = the walker alone; 0 = the library's choice)")
     ap.add_argument("--prune-gap", type=int, default=0,
                     help="integer modes: early-INF pruning of cells whose samples differ by more than this")
     ap.add_argument("--keep-checkpoints", action="store_true",
@@ -64,7 +66,8 @@ def main():
                       max_total_query_len=qs.numel(), grad=a.backward or a.keep_checkpoints,
                       keep_checkpoints=a.backward or a.keep_checkpoints,
                       seg_width=a.seg_width, warps_per_query=a.warps, tile_rows=a.tile_rows,
-                      ckpt_stride=a.ckpt_stride, prune_gap=a.prune_gap)
+                      ckpt_stride=a.ckpt_stride, prune_gap=a.prune_gap,
+                      bwd_warps=a.bwd_warps)
     if a.autotune:
         ctx.autotune(ref, qs, offsets=offs, N=N if offs is not None else None)
     Nr = N if offs is not None else None

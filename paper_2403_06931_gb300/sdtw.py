@@ -35,7 +35,8 @@ class SdtwContext:
                  max_batch: int = 512, max_query_len: int = 2000, max_total_query_len: int | None = None,
                  grad: bool = False, keep_checkpoints: bool = False, seg_width: int = 0,
                  warps_per_query: int = 0, ckpt_stride: int = 0, mem_cap_bytes: int = 0, tile_rows: int = 0,
-                 znorm_queries: bool = False, check_status: bool = True, prune_gap: int = 0):
+                 znorm_queries: bool = False, check_status: bool = True, prune_gap: int = 0,
+                 bwd_warps: int = 0):
         lib_dtype = {"f32": capi.SDTW_F32, "i8": capi.SDTW_I8, "u8": capi.SDTW_U8, "f16": capi.SDTW_F16}[dtype]
         cfg = capi.sdtw_config_init()
         cfg.dtype = lib_dtype
@@ -49,6 +50,7 @@ class SdtwContext:
         cfg.ckpt_stride = int(ckpt_stride)
         cfg.mem_cap_bytes = int(mem_cap_bytes)
         cfg.tile_rows = int(tile_rows)
+        cfg.bwd_warps = int(bwd_warps)
         cfg.prune_gap = int(prune_gap)
         cfg.flags = (capi.SDTW_FLAG_GRAD if grad or keep_checkpoints else 0) | \
             (capi.SDTW_FLAG_KEEP_CHECKPOINTS if keep_checkpoints else 0) | \

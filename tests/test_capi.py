@@ -173,6 +173,13 @@ def test_prune_gap_accepted_only_for_integer_modes(lib):
         assert capi.sdtw_create(cfg)[0] == want, (dtype, gap)
 
 
+def test_backward_warps_range(lib):
+    for v in (-1, 5, 32):
+        cfg = capi.sdtw_config_init()
+        cfg.bwd_warps = v
+        assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_INVALID, v
+
+
 def test_eight_row_tiles_only_for_plain_fills_of_16_to_28_columns(lib):
     for dtype, flags, width in ((capi.SDTW_F32, capi.SDTW_FLAG_GRAD, 0), (capi.SDTW_F32, 0, 32), (capi.SDTW_F32, 0, 8),
                                 (capi.SDTW_I8, 0, 32), (capi.SDTW_U8, 0, 8), (capi.SDTW_F16, 0, 32)):

@@ -193,6 +193,26 @@ def test_backward_ragged(gpu):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
 
 
+@pytest.mark.parametrize("case", ["stretched16", "stretched64", "tiny_rt2", "w8", "ragged", "vertical"])
+def test_backward_helpers_give_identical_results(gpu, case):
+    # the walker alone (bwd_warps=1) and with 1 to 3 helpers recomputing the
+    # predicted bands: the same path, gradients and reference gradient, bit for bit
+    w, st = {
+        "stretched16": (inputs.stretched(B=6, N=300, M=30000, scale=8.0), dict(ckpt_stride=16)),
+        "stretched64": (inputs.stretched(B=4, N=300, M=30000), dict(ckpt_stride=64, tile_rows=2)),
+        "tiny_rt2": (inputs.tiny(B=5, N=500, M=8000, seed=91), dict(seg_width=24, tile_rows=2, warps_per_query=3)),
+        "w8": (inputs.tiny(B=4, N=400, M=6000, seed=92), dict(seg_width=8, tile_rows=4, warps_per_query=2)),
+        "ragged": (inputs.ragged_fp32(B=9, n_lo=1, n_hi=500, M=7000, seed=93), {}),
+        "vertical": (inputs.tiny(B=2, N=2500, M=300, seed=61), dict(seg_width=8, tile_rows=2, warps_per_query=1)),
+    }[case]
+    runs = [run_bwd(gpu, w, bwd_warps=k, **st) for k in (1, 2, 3, 4)]
+    for r in runs[1:]:
+        for k in range(5):
+            assert np.array_equal(runs[0][k], r[k]), k
+    oc, _ = oracle.forward_batch(w.ref, w.queries, offsets=w.offsets)
+    check_validity(w, *runs[3], range(w.B), oc)
+
+
 def _ckpt_floats_per_query(M, N, W, P, RT, KS):
     """Backward workspace per query (floats) of a checkpointing plan: the
     wavefront slot (one record of W + 4 or W + 8 floats per thread and
@@ -377,3 +397,7 @@ def test_paper_batch_backward_full_size(gpu):
     idx = sorted(np.random.default_rng(5).choice(w.B, size=12, replace=False).tolist())
     oc, _ = oracle.forward_batch(w.ref, w.queries, indices=idx)
     check_validity(w, cost, end, gq, gr, path, g, idx, oc)
+    # the library's choice of helpers against the walker alone: identical
+    alone = run_bwd(gpu, w, bwd_warps=1)
+    for k, v in enumerate((cost, end, gq, gr, path)):
+        assert np.array_equal(v, alone[k]), k
