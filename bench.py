@@ -39,15 +39,17 @@ OPS_PER_CELL = 6          # instruction-issue roofline: ops per DP cell (subtrac
 LANES_PER_SM = 128        # 4 schedulers x 32 lanes
 L2_FLUSH_BYTES = 512 << 20
 
-# ncu DRAM traffic of one checkpointing forward launch on the paper batch, valid
-# only while the forward kernel's code hashes to FWD_SRC_SHA (else reported as
-# null).  Captured on 128 of the 512 queries with the default plan (32 columns x
-# 4 rows per thread, a checkpoint every 16 steps; 2,444,288 bytes read +
-# 2,387,886,848 written: the writes are the per-query checkpoints) and scaled by
-# 4 to the 512-query launch;
+# ncu DRAM traffic of one checkpointing forward launch on the paper batch, per
+# plan (seg_width, tile_rows, warps_per_query, ckpt_stride), valid only while
+# the forward kernel's code hashes to FWD_SRC_SHA (else, or for another plan,
+# reported as null).  Captured on 128 of the 512 queries (the writes are the
+# per-query checkpoints) and scaled by 4 to the 512-query launch;
 # profiles/fwd_chain_kernel_f32_ckpt_W32_RT4_KS16_paper_512x2000_vs_100000.md
 FWD_SRC_SHA = "f2eb11686c846bca"
-FWD_TRAFFIC_BYTES = 4 * (2_444_288 + 2_387_886_848)
+FWD_TRAFFIC_BYTES = {
+    (32, 4, 4, 16): 4 * (2_444_288 + 2_387_886_848),
+    (32, 4, 4, 32): 4 * (1_959_424 + 1_363_876_864),
+}
 
 
 def src_sha(*paths):
@@ -194,7 +196,9 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     ctx = SdtwContext(max_ref_len=M, max_batch=B, max_query_len=N, grad=True, keep_checkpoints=True)
-    tuned = ctx.plan(B, N, M) if args.no_autotune else ctx.autotune(ref, qs)
+    if not args.no_autotune:
+        ctx.autotune(ref, qs)
+    tuned = ctx.plan(B, N, M, backward=True)
     h = ctx.handle
     P = lambda t: t.data_ptr()  # noqa: E731
 
@@ -292,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = cells / (fwd_avg * 1e-3) / 1e9
     csrc = os.path.join(ROOT, "paper_2403_06931_gb300", "csrc")
     fwd_sha = src_sha(os.path.join(csrc, "sdtw_fill.cuh"), os.path.join(csrc, "sdtw_cell.cuh"))
-    traffic = FWD_TRAFFIC_BYTES if FWD_SRC_SHA == fwd_sha else None
+    pkey = (tuned["seg_width"], tuned["tile_rows"], tuned["warps_per_query"], tuned["ckpt_stride"])
+    traffic = FWD_TRAFFIC_BYTES.get(pkey) if FWD_SRC_SHA == fwd_sha else None
     roof = {"bound": "alu", "kernel": "fwd_chain_kernel", "achieved": round(achieved, 1),
             "peak": round(peak_gcups, 1), "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4),
             "traffic": traffic,

@@ -86,6 +86,10 @@ typedef enum sdtw_dtype {
  * query that would reach past it is skipped and reported like a query longer
  * than N. */
 #define SDTW_FLAG_ZNORM_QUERIES 0x8u
+/* For tests of the device-side timeout only: the backward's helper warps take no
+ * work, so the walker's bounded wait for a band it handed out runs out and
+ * sdtw_last_device_status reports SDTW_E_TIMEOUT (after about 2 s). */
+#define SDTW_FLAG_TEST_IDLE_HELPERS 0x10u
 
 typedef struct sdtw_config {
     sdtw_dtype dtype;

@@ -32,6 +32,7 @@ SDTW_FLAG_GRAD = 0x1
 SDTW_FLAG_KEEP_CHECKPOINTS = 0x2
 SDTW_FLAG_NO_AUTOTUNE = 0x4
 SDTW_FLAG_ZNORM_QUERIES = 0x8
+SDTW_FLAG_TEST_IDLE_HELPERS = 0x10
 
 ABI_VERSION = 5
 

@@ -566,6 +566,7 @@ cudaError_t launch_bwd(sdtw_ctx* ctx, const FwdPlan& p, const CkPtrs& ck, const 
     a.KS = p.KS;
     a.rebase_period = sdtw::ckpt_rebase_period(p.KS);
     a.warps = ctx->cfg.bwd_warps;
+    a.idle_helpers = (ctx->cfg.flags & SDTW_FLAG_TEST_IDLE_HELPERS) ? 1 : 0;
     a.gyq = ck.gyq;
     a.span = ck.span;
     a.status = ctx->d_status;

@@ -443,6 +443,7 @@ __global__ void __launch_bounds__(32 * kMaxSlots) bwd_band_kernel(const BwdArgs 
 
     if (warp > 0) {
         // ---- a helper: recompute the bands handed to it until the walk ends
+        if (a.idle_helpers) return;  // tests of the walker's bounded wait
         const int h = warp - 1;
         float Dd[WB], Bd;
         long long t_idle = global_ns();  // lane 0: when this helper last had work

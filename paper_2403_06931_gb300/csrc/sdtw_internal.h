@@ -139,6 +139,7 @@ struct BwdArgs {
     int32_t KS;             // steps between the forward's wavefront checkpoints: a band's height in steps
     int32_t rebase_period;  // the forward's steps between rebases
     int32_t warps;          // warps per query: 1 = the walker alone, 2..4 with helpers, 0 = the library's choice
+    int32_t idle_helpers;   // tests only: the helpers take no work (the walker's wait runs out)
     float* gyq;      // [B][M] per-query reference gradient rows (only the path span is written)
     int64_t* span;   // [B][2] first and last column of each query's path
     int* status;

@@ -36,7 +36,7 @@ class SdtwContext:
                  grad: bool = False, keep_checkpoints: bool = False, seg_width: int = 0,
                  warps_per_query: int = 0, ckpt_stride: int = 0, mem_cap_bytes: int = 0, tile_rows: int = 0,
                  znorm_queries: bool = False, check_status: bool = True, prune_gap: int = 0,
-                 bwd_warps: int = 0):
+                 bwd_warps: int = 0, extra_flags: int = 0):
         lib_dtype = {"f32": capi.SDTW_F32, "i8": capi.SDTW_I8, "u8": capi.SDTW_U8, "f16": capi.SDTW_F16}[dtype]
         cfg = capi.sdtw_config_init()
         cfg.dtype = lib_dtype
@@ -54,7 +54,7 @@ class SdtwContext:
         cfg.prune_gap = int(prune_gap)
         cfg.flags = (capi.SDTW_FLAG_GRAD if grad or keep_checkpoints else 0) | \
             (capi.SDTW_FLAG_KEEP_CHECKPOINTS if keep_checkpoints else 0) | \
-            (capi.SDTW_FLAG_ZNORM_QUERIES if znorm_queries else 0)
+            (capi.SDTW_FLAG_ZNORM_QUERIES if znorm_queries else 0) | int(extra_flags)
         st, h = capi.sdtw_create(cfg)
         capi.check(st, "sdtw_create")
         self.handle = h

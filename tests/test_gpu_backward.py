@@ -213,6 +213,24 @@ def test_backward_helpers_give_identical_results(gpu, case):
     check_validity(w, *runs[3], range(w.B), oc)
 
 
+def test_walker_wait_runs_out_when_helpers_never_answer(gpu):
+    # a test flag keeps the helper warps from taking work: the walker's wait for
+    # a band it handed out ends at its time limit (about 2 s) with SDTW_E_TIMEOUT
+    # in the device status, and the device stays usable
+    w = inputs.stretched(B=4, N=300, M=30000)
+    ref = torch.from_numpy(w.ref).to(gpu)
+    qs = torch.from_numpy(w.queries).to(gpu)
+    ctx = SdtwContext(max_ref_len=w.M, max_batch=w.B, max_query_len=w.N, grad=True, keep_checkpoints=True,
+                      bwd_warps=3, extra_flags=capi.SDTW_FLAG_TEST_IDLE_HELPERS)
+    cost, end = ctx.forward(ref, qs)
+    ctx.backward(ref, qs, end, torch.ones(w.B, device=gpu))
+    assert ctx.device_status() == capi.SDTW_E_TIMEOUT
+    ctx.close()
+    cost, end, gq, gr, path, g = run_bwd(gpu, w)     # a fresh context works (its status is checked)
+    oc, _ = oracle.forward_batch(w.ref, w.queries)
+    check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
+
+
 def _ckpt_floats_per_query(M, N, W, P, RT, KS):
     """Backward workspace per query (floats) of a checkpointing plan: the
     wavefront slot (one record of W + 4 or W + 8 floats per thread and
