@@ -70,8 +70,6 @@ struct DirWord<7> { using T = uint16_t; };
 template <>
 struct DirWord<8> { using T = uint16_t; };
 
-constexpr int kDiag = 0, kLeft = 1, kUp = 2, kOutside = 3;
-
 // Rows a lane advances per step of the band recompute, for bands of tiles of
 // RT rows: more rows give the lane more independent dependency chains, but
 // lengthen the 32-step fill and drain of the lane chain.
@@ -135,6 +133,9 @@ struct Band {
 // The forward's schedule for one query (sdtw_fill.cuh)
 struct Sched {
     int n, nt, Pp, S, KS;
+    int wps;     // windows per sweep, S / K = 4 P
+    float rwps;  // 1 / wps
+    int kslog;   // log2 KS (16, 32 or 64)
 };
 
 template <int WB, int RT>
@@ -144,11 +145,15 @@ __device__ __forceinline__ Band band_at(const Sched& sc, int wi, int wj)
     Band g;
     g.b = wj / KW;
     g.c0 = g.b * KW;
-    const int s = g.c0 / sc.S;
-    g.tau0 = (g.c0 - s * sc.S) / W;
+    // the sweep s = b / wps without an integer division (b < 2^24: the float
+    // quotient is off by at most one)
+    int s = __float2int_rz(static_cast<float>(g.b) * sc.rwps);
+    s += (s + 1) * sc.wps <= g.b;
+    s -= s * sc.wps > g.b;
+    g.tau0 = 8 * (g.b - s * sc.wps);  // (c0 - s S) / W, as K = 8 W
     const int lag0 = (g.tau0 >> 5) * (32 + kChunk) + (g.tau0 & 31);  // strips of a window share a warp
     const int dj = (wj - g.c0) / W;
-    g.c = (wi / RT + lag0 + dj + s * sc.Pp) / sc.KS;
+    g.c = (wi / RT + lag0 + dj + s * sc.Pp) >> sc.kslog;
     g.ps0 = g.c * sc.KS - lag0 - s * sc.Pp;
     g.rtop = RT * (g.ps0 - 7);
     return g;
@@ -330,6 +335,7 @@ __device__ __forceinline__ int recompute_band(const BwdArgs& a, const Sched& sc,
 // Shared-memory bookkeeping of the band slots: per slot its state, the band
 // (window b, checkpoint c) and the cell it was computed for (rows down to wi,
 // strips 0..dj), and the first step of its choice rows.
+constexpr int kDiag = 0, kLeft = 1, kUp = 2, kOutside = 3;  // a cell's walk-back choice
 constexpr int kSlotFree = 0, kSlotAssigned = 1, kSlotReady = 2, kSlotOwn = 3;
 constexpr int kMetaInts = 8;  // state, b, c, wi, wj, dj, sg0, spare
 constexpr int kMaxSlots = 4;
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(32 * kMaxSlots) bwd_band_kernel(const BwdArgs 
     // the forward's schedule for this query (sdtw_fill.cuh)
     const int lag_last = (a.P - 1) * (32 + kChunk) + 31;
     const int nt = (n + RT - 1) / RT;
-    const Sched sc{n, nt, max(nt, lag_last + kChunk), 32 * a.P * W, KS};
+    const Sched sc{n, nt, max(nt, lag_last + kChunk), 32 * a.P * W, KS, 4 * a.P, 1.f / (4 * a.P), __ffs(KS) - 1};
     const float* frq = a.fr + static_cast<int64_t>(ql) * a.fr_slot;
     const float* ckq = a.colck + static_cast<int64_t>(ql) * a.ck_slot;
 
@@ -516,74 +522,104 @@ __global__ void __launch_bounds__(32 * kMaxSlots) bwd_band_kernel(const BwdArgs 
             give_up(kStatusReplay);  // the current cell is not in its band
             return;
         }
-        // a slot that holds it (a helper's), else the walker recomputes it
-        // into the slot of the band it leaves (the walk never returns to a band)
-        int use = -1;
-        for (int s2 = 0; s2 < NS; ++s2) {
-            const volatile int* m = meta + s2 * kMetaInts;
-            if (s2 != cur && m[0] != kSlotFree && m[1] == g.b && m[2] == g.c && m[3] >= wi && m[5] >= dj) use = s2;
+        // Slot bookkeeping, lane-parallel: lane s < NS reads slot s, ballots
+        // combine the lanes' findings, and lane 0 writes hand-outs.
+        // A slot that holds this band (a helper's), else the walker recomputes
+        // it into the slot of the band it leaves (the walk never returns to a band)
+        const bool slot_lane = lane < NS;
+        int st_l = kSlotOwn, kb = -1, kc = -1, kw = -1, kd = -1;  // lane s: slot s's state and band
+        if (slot_lane) {
+            const volatile int* m = meta + lane * kMetaInts;
+            st_l = m[0];
+            kb = m[1];
+            kc = m[2];
+            kw = m[3];
+            kd = m[5];
         }
-        const bool hit = use >= 0;
-        if (lane == 0) meta[cur * kMetaInts] = hit ? kSlotFree : kSlotOwn;
-        if (hit) cur = use;
-        __syncwarp();
-        // the bands a path staying on row wi would visit next, for the idle
-        // helpers; finished slots that no prediction names are freed.  Run at
-        // band entry (so that the helpers work during the walker's own
-        // recompute or wait) and again once the band is ready (a helper that
-        // finished meanwhile takes the next prediction at once)
-        auto predict = [&]() {
-            if (H == 0 || lane != 0) return;
-            int pb[kMaxSlots], pc[kMaxSlots], pj[kMaxSlots];
-            bool have[kMaxSlots];
-            int np = 0;
+        const unsigned found = __ballot_sync(0xffffffffu, slot_lane && lane != cur && st_l != kSlotFree &&
+                                                              kb == g.b && kc == g.c && kw >= wi && kd >= dj);
+        const bool hit = found != 0u;
+        if (lane == cur) {
+            st_l = hit ? kSlotFree : kSlotOwn;
+            meta[cur * kMetaInts] = st_l;
+        }
+        if (hit) cur = __ffs(found) - 1;
+        // the bands a path staying on row wi would visit next, left of this one
+        int pb[kMaxSlots - 1], pc[kMaxSlots - 1], pj[kMaxSlots - 1];
+        int np = 0;
+        {
             int jj = c0 + max(0, ps0 - wi / RT) * W - 1;  // left of the band's leftmost cell of row wi
-            while (np < H && jj >= 0) {
-                const Band gp = band_at<WB, RT>(sc, wi, jj);
-                pb[np] = gp.b;
-                pc[np] = gp.c;
-                pj[np] = jj;
-                have[np] = false;
-                ++np;
-                jj = gp.c0 + max(0, gp.ps0 - wi / RT) * W - 1;
+#pragma unroll
+            for (int k = 0; k < kMaxSlots - 1; ++k) {
+                pb[k] = pc[k] = pj[k] = -1;
+                if (k < H && jj >= 0) {
+                    const Band gp = band_at<WB, RT>(sc, wi, jj);
+                    pb[k] = gp.b;
+                    pc[k] = gp.c;
+                    pj[k] = jj;
+                    np = k + 1;
+                    jj = gp.c0 + max(0, gp.ps0 - wi / RT) * W - 1;
+                } else {
+                    jj = -1;
+                }
             }
-            for (int s2 = 0; s2 < NS; ++s2) {
-                volatile int* m = meta + s2 * kMetaInts;
-                const int st = m[0];
-                if (s2 == cur || st == kSlotFree) continue;
-                bool named = false;
-                for (int k = 0; k < np; ++k)
-                    if (m[1] == pb[k] && m[2] == pc[k] && m[3] >= wi && m[5] >= 7) {
-                        have[k] = true;
-                        named = true;
-                    }
-                // a finished band no prediction names is dropped (a helper's band
-                // in flight runs to its end: stopping it measured slower, as such
-                // bands are often visited after all)
-                if (!named && st == kSlotReady) m[0] = kSlotFree;
+        }
+        // hand the predicted bands that no slot holds to idle helpers; finished
+        // slots that no prediction names are freed.  Run at band entry (so that
+        // the helpers work during the walker's own recompute or wait) and again
+        // once the band is ready (a helper that finished meanwhile takes the
+        // next prediction at once)
+        auto predict = [&](bool reread) {
+            if (H == 0) return;
+            if (reread && slot_lane && lane != cur) st_l = meta[lane * kMetaInts];
+            const bool mine = slot_lane && lane != cur && st_l != kSlotFree && st_l != kSlotOwn;
+            bool named = false;
+            unsigned have = 0u;
+#pragma unroll
+            for (int k = 0; k < kMaxSlots - 1; ++k) {
+                const bool nk = mine && k < np && kb == pb[k] && kc == pc[k] && kw >= wi && kd >= 7;
+                named |= nk;
+                if (__ballot_sync(0xffffffffu, nk)) have |= 1u << k;
             }
-            for (int k = 0; k < np; ++k) {
-                if (have[k]) continue;
-                int fs = -1, fh = -1;
-                for (int s2 = 0; s2 < NS; ++s2)
-                    if (s2 != cur && meta[s2 * kMetaInts] == kSlotFree) fs = s2;
-                for (int h2 = 0; h2 < H; ++h2)
-                    if (mailbox[h2] < 0) fh = h2;
-                if (fs < 0 || fh < 0) break;
-                volatile int* m = meta + fs * kMetaInts;
-                m[1] = pb[k];
-                m[2] = pc[k];
-                m[3] = wi;
-                m[4] = pj[k];
-                m[5] = 7;
-                m[6] = -1;
-                __threadfence_block();
-                m[0] = kSlotAssigned;
-                __threadfence_block();
-                mailbox[fh] = fs;
+            // a finished band no prediction names is dropped (a helper's band in
+            // flight runs to its end: stopping it measured slower, as such bands
+            // are often visited after all)
+            if (mine && !named && st_l == kSlotReady) {
+                st_l = kSlotFree;
+                meta[lane * kMetaInts] = kSlotFree;
+            }
+            unsigned fm = __ballot_sync(0xffffffffu, slot_lane && lane != cur && st_l == kSlotFree);
+            unsigned im = __ballot_sync(0xffffffffu, lane < H && mailbox[lane < H ? lane : 0] < 0);
+#pragma unroll
+            for (int k = 0; k < kMaxSlots - 1; ++k) {
+                if (k >= np || (have >> k) & 1u || fm == 0u || im == 0u) continue;
+                const int fs = __ffs(fm) - 1, fh = __ffs(im) - 1;
+                fm &= fm - 1u;
+                im &= im - 1u;
+                if (lane == fs) {
+                    // this lane's view of its slot follows the hand-out
+                    st_l = kSlotAssigned;
+                    kb = pb[k];
+                    kc = pc[k];
+                    kw = wi;
+                    kd = 7;
+                }
+                if (lane == 0) {
+                    volatile int* m = meta + fs * kMetaInts;
+                    m[1] = pb[k];
+                    m[2] = pc[k];
+                    m[3] = wi;
+                    m[4] = pj[k];
+                    m[5] = 7;
+                    m[6] = -1;
+                    __threadfence_block();
+                    m[0] = kSlotAssigned;
+                    __threadfence_block();
+                    mailbox[fh] = fs;
+                }
             }
         };
-        predict();
+        predict(false);
         __syncwarp();
 
         int sg0;
@@ -614,7 +650,7 @@ __global__ void __launch_bounds__(32 * kMaxSlots) bwd_band_kernel(const BwdArgs 
             give_up(kStatusReplay);  // the band's steps exceed the slot
             return;
         }
-        predict();
+        predict(true);
         __syncwarp();
         const float* ys = slot_ys(cur);
         const DW* dirs = slot_dirs(cur);

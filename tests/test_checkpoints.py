@@ -664,3 +664,46 @@ def test_rebase_to_low_left_inputs_is_replayed(P, W, RT, KS):
     cells, v_end, _ = kernel_backward(fw, pl, fw["end"])
     assert v_end == fw["cost"]
     assert cells == _walk(lambda i, j: fw["D"][(i, j)][2], pl.n, fw["end"])
+
+
+def _dir_rows(RT, KS, RS=2):
+    """The band-slot size the library reserves (bwd_dir_rows in the backward):
+    RS rows per step from the earliest first step (RT*7/RS) to the latest last
+    step of a band (over every entry strip dj)."""
+    most = max((RT * (KS + 7 - dj) - 1) // RS + 4 * dj + 4 for dj in range(8))
+    return RS * (most - RT * 7 // RS)
+
+
+@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("KS", [16, 32, 64])
+def test_band_slot_rows_bound(RT, KS):
+    # the backward's lane schedule for a band: lane l (strip d = l // 4) has rows
+    # [rf, hi) and handles row r at step (r - rtop) / RS + l; the band starts at
+    # the first step any lane has a row (sg0) and, for an entry cell (wi, strip
+    # dj), ends after the last step at which a lane of strips 0..dj has one
+    # (the walker: dj = the entry strip; a helper: dj = 7).  Every band of every
+    # geometry must fit the reserved rows, and the bound must be reached.
+    RS = 2
+    bound, worst = _dir_rows(RT, KS), 0
+    for n in (1, 37, 64, 2000):
+        nt = (n + RT - 1) // RT
+        for ps0 in range(-KS - 3, min(nt, 3 * KS) + 3):
+            rtop = RT * (ps0 - 7)
+            for wi in range(max(0, rtop), min(n, RT * (ps0 + KS + 1))):
+                inside = [RT * max(0, ps0 - d) <= wi < min(n, RT * min(nt, ps0 - d + KS)) for d in range(8)]
+                for dj in [d for d in range(8) if inside[d]] + ([7] if any(inside) else []):
+                    firsts, lasts = [], []
+                    for lane in range(32):
+                        d = lane >> 2
+                        rf = RT * max(0, ps0 - d)
+                        hi = min(min(n, RT * min(nt, ps0 - d + KS)), wi + 1)
+                        if rf < hi:
+                            firsts.append((rf - rtop) // RS + lane)
+                            if d <= dj:
+                                lasts.append((hi - 1 - rtop) // RS + lane)
+                    steps = 1 + (max(lasts) if lasts else 0)
+                    sg0 = min(firsts) if firsts else steps
+                    need = RS * max(0, steps - sg0)
+                    assert need <= bound, (RT, KS, n, ps0, wi, dj, need, bound)
+                    worst = max(worst, need)
+    assert worst == bound
