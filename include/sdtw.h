@@ -101,7 +101,7 @@ typedef struct sdtw_config {
     int32_t seg_width;           /* reference columns per thread (the paper's segment width): 8, 16, 20, 24, 28
                                     or 32; 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
-    int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints: 16, 32 or 64; 0 = chosen by
+    int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints: 8, 16, 32 or 64; 0 = chosen by
                                     the library (16, or the autotuner's choice) */
     int32_t prune_gap;           /* SDTW_I8 / SDTW_U8 only: 0 = off (exact); > 0 = early-INF pruning (paper
                                     Section 8, opt-in, changes results): a cell whose two samples differ by more
@@ -111,9 +111,9 @@ typedef struct sdtw_config {
     uint64_t spin_limit;         /* reserved, must be 0 (the backward's helpers wait on flags in shared memory with
                                     a fixed limit of 2 s each) */
     uint32_t flags;              /* SDTW_FLAG_* */
-    int32_t tile_rows;           /* query rows a thread advances per step: 2 or 4, or 8 for the plain fills
-                                    (any dtype without SDTW_FLAG_GRAD, seg_width 16 to 28); 0 = chosen by the
-                                    library */
+    int32_t tile_rows;           /* query rows a thread advances per step: 2 or 4, or 8 with
+                                    seg_width 16 to 28 (any dtype; with checkpoints, SDTW_F32); 0 = chosen by
+                                    the library */
     int32_t bwd_warps;           /* warps per query in sdtw_backward and sdtw_path: 1 = one warp walks the path
                                     and recomputes every band; 2 to 4 = that warp and 1 to 3 helpers that
                                     recompute the bands a path staying on its current row would visit next;
@@ -155,10 +155,10 @@ sdtw_status sdtw_config_init(sdtw_config* cfg);
  * *out receives the context, or NULL on error.
  * Errors: SDTW_E_INVALID (NULL arguments, non-positive maxima, unknown dtype,
  * SDTW_FLAG_GRAD with a dtype other than SDTW_F32, an unsupported seg_width or
- * tile_rows (8 with SDTW_FLAG_GRAD or a seg_width outside 16 to 28), a
+ * tile_rows (8 with a seg_width outside 16 to 28), a
  * non-zero spin_limit, a negative ckpt_stride or prune_gap, a prune_gap with
  * SDTW_F32 or SDTW_F16, a bwd_warps outside 0 to 4),
- * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 16, 32 or 64, or a
+ * SDTW_E_UNSUPPORTED (a ckpt_stride other than 0, 8, 16, 32 or 64, or a
  * max_query_len no forward plan can stage in shared memory),
  * SDTW_E_NOMEM (workspace above mem_cap_bytes, too small for one query's
  * checkpoints, or allocation failure), SDTW_E_CUDA (device unusable). */
@@ -205,7 +205,7 @@ sdtw_status sdtw_forward(sdtw_ctx* ctx, const void* ref, int64_t M, const void* 
  * smallest D, exact ties to the first of that list, column 0 upwards, stopping
  * at row 0).  The DP is recomputed band by band from checkpoints of the
  * forward: its wavefront (an anti-diagonal staircase of rows, one per thread)
- * every ckpt_stride steps (16, 32 or 64), and the boundary column of every
+ * every ckpt_stride steps (8, 16, 32 or 64), and the boundary column of every
  * K-column window (K = 8 * seg_width); a band (one window, one stride of
  * steps) is recomputed with the forward's own FP32 operations, so the values
  * are the forward's bit for bit.  A shorter stride makes each band change of
@@ -285,7 +285,7 @@ sdtw_status sdtw_forward_backward_host(sdtw_ctx* ctx, const float* ref, int64_t 
  * the batch's checkpoints, each candidate is timed as a forward with
  * checkpoint stores followed by the backward (with zero upstream gradients
  * into scratch it allocates for the call), so the plan serves the
- * differentiable step; the checkpoint stride (16, 32 or 64 steps, unless the
+ * differentiable step; the checkpoint stride (8, 16, 32 or 64 steps, unless the
  * config fixes it) is then one more axis, and a stride whose checkpoints do
  * not fit the workspace under mem_cap_bytes is not a candidate.  Runs several forwards on `stream` and synchronises
  * it.  Arguments as sdtw_forward; cost/end are scratch outputs.  *plan (if not

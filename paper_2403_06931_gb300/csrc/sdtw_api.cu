@@ -29,7 +29,7 @@ constexpr int kI8MaxN = sdtw::kIntMaxN;
 // the backward's recompute per band change short
 constexpr int kDefaultStride = 16;
 // the strides the autotuner times for a context that keeps checkpoints
-constexpr int kStrides[] = {16, 32, 64};
+constexpr int kStrides[] = {8, 16, 32, 64};
 
 struct DevBuf {
     void* p = nullptr;
@@ -156,11 +156,13 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
     // checkpoints with 4-row tiles of 32 columns (the backward's wider windows
     // give fewer band changes)
     FwdPlan p;
-    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width : (ckpt ? 32 : int_mode(c->cfg.dtype) ? 28 : 24);
+    p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width
+                               : (ckpt ? (c->cfg.tile_rows == 8 ? 28 : 32) : int_mode(c->cfg.dtype) ? 28 : 24);
     p.P = c->cfg.warps_per_query > 0 ? c->cfg.warps_per_query : 4;
     p.RT = c->cfg.tile_rows > 0 ? c->cfg.tile_rows
                                 : (sdtw::fwd_plan_supported(c->cfg.dtype, p.W, 8, ckpt) && c->cfg.prune_gap == 0 ? 8 : 4);
-    p.KS = c->cfg.ckpt_stride > 0 ? c->cfg.ckpt_stride : kDefaultStride;
+    // 64-row bands: 8 steps of 8-row tiles, 16 of 4-row tiles
+    p.KS = c->cfg.ckpt_stride > 0 ? c->cfg.ckpt_stride : (p.RT == 8 ? 8 : kDefaultStride);
     auto it = c->tuned.find(TuneKey{c->cfg.dtype, ragged ? 1 : 0, bucket_of(N), bucket_of(M), ckpt ? 1 : 0});
     if (it != c->tuned.end()) {
         if (c->cfg.seg_width <= 0) p.W = std::get<0>(it->second);
@@ -441,10 +443,9 @@ sdtw_status sdtw_create(sdtw_ctx** out, const sdtw_config* cfg)
     if ((cfg->flags & SDTW_FLAG_ZNORM_QUERIES) && cfg->dtype != SDTW_F32) return SDTW_E_INVALID;
     if (cfg->seg_width > 0 && !sdtw::fwd_width_supported(cfg->dtype, cfg->seg_width)) return SDTW_E_INVALID;
     if (cfg->tile_rows != 0 && cfg->tile_rows != 2 && cfg->tile_rows != 4 && cfg->tile_rows != 8) return SDTW_E_INVALID;
-    // 8-row tiles: plain fills only (no checkpoints), 16 to 28 columns
-    if (cfg->tile_rows == 8 &&
-        ((cfg->flags & SDTW_FLAG_GRAD) ||
-         (cfg->seg_width > 0 && !sdtw::fwd_plan_supported(cfg->dtype, cfg->seg_width, 8, false))))
+    // 8-row tiles: 16 to 28 columns
+    if (cfg->tile_rows == 8 && cfg->seg_width > 0 &&
+        !sdtw::fwd_plan_supported(cfg->dtype, cfg->seg_width, 8, (cfg->flags & SDTW_FLAG_GRAD) != 0))
         return SDTW_E_INVALID;
     if (cfg->ckpt_stride < 0 || cfg->prune_gap < 0 || cfg->spin_limit != 0) return SDTW_E_INVALID;
     if (cfg->bwd_warps < 0 || cfg->bwd_warps > 4) return SDTW_E_INVALID;

@@ -8,7 +8,7 @@
 //   d cost / d y_j = sum over the path's cells in column j of -2 (x_i - y_j).
 //
 // The n x M matrix is never stored.  The checkpointing forward left, at the
-// start of every KS-th step (KS = 16, 32 or 64), its wavefront (each thread's latest
+// start of every KS-th step (KS = 8, 16, 32 or 64), its wavefront (each thread's latest
 // row, the right-hand cells of its tile's other rows, its diagonal input and
 // its integer base: an anti-diagonal staircase of rows, stored before a
 // rebase due at that step, which is redone here), and the left inputs of every
@@ -135,7 +135,7 @@ struct Sched {
     int n, nt, Pp, S, KS;
     int wps;     // windows per sweep, S / K = 4 P
     float rwps;  // 1 / wps
-    int kslog;   // log2 KS (16, 32 or 64)
+    int kslog;   // log2 KS (8, 16, 32 or 64)
 };
 
 template <int WB, int RT>
@@ -205,7 +205,7 @@ __device__ __forceinline__ int recompute_band(const BwdArgs& a, const Sched& sc,
     // column); a checkpoint between rebases is already in its base
     const bool redo = (g.c * KS) % a.rebase_period == 0;
     auto rebase = [&](int th, float& bn, float& dl) {
-        const float b0 = rec_at(RT == 2 ? 2 : 4, th);
+        const float b0 = rec_at(RT, th);  // the record: RT-1 right-hand cells, diag, base
         bn = redo ? floorf(b0 + fr_at(0, th)) : b0;
         dl = bn - b0;
     };
@@ -782,7 +782,11 @@ cudaError_t launch_walk_wb(const BwdArgs& a, cudaStream_t s)
     const int warps = bwd_warps(a.N, 4 * WB, a.RT, a.KS, a.warps);
     if (warps < 1) return cudaErrorInvalidValue;
     const int smem = static_cast<int>(bwd_smem_bytes(a.N, 4 * WB, a.RT, a.KS, warps));
-    auto k = a.RT == 2 ? bwd_band_kernel<WB, 2, rows_per_step(2)> : bwd_band_kernel<WB, 4, rows_per_step(4)>;
+    auto k = bwd_band_kernel<WB, 4, rows_per_step(4)>;
+    if (a.RT == 2) k = bwd_band_kernel<WB, 2, rows_per_step(2)>;
+    if constexpr (WB >= 4 && WB <= 7) {  // 8-row tiles: segments of 16 to 28 columns
+        if (a.RT == 8) k = bwd_band_kernel<WB, 8, rows_per_step(8)>;
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -832,7 +836,8 @@ int bwd_warps(int64_t N, int W, int RT, int KS, int requested)
 cudaError_t launch_backward_walk(const BwdArgs& a, cudaStream_t s)
 {
     if (a.B <= 0) return cudaSuccess;
-    if (a.K != 8 * a.W || (a.RT != 2 && a.RT != 4) || !ckpt_stride_supported(a.KS) ||
+    if (a.K != 8 * a.W || (a.RT != 2 && a.RT != 4 && !(a.RT == 8 && a.W >= 16 && a.W <= 28)) ||
+        !ckpt_stride_supported(a.KS) ||
         a.rebase_period != ckpt_rebase_period(a.KS))
         return cudaErrorInvalidValue;
     switch (a.W) {

@@ -326,10 +326,12 @@ __device__ __forceinline__ bool rebase_to_left(float (&prev)[W], float& diag, fl
 template <int RT>
 __device__ __forceinline__ void store_rows(float* dst, const float (&v)[RT])
 {
-    if constexpr (RT == 2)
+    if constexpr (RT == 2) {
         __stcs(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
-    else
+    } else {
         __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+        if constexpr (RT == 8) __stcs(reinterpret_cast<float4*>(dst) + 1, make_float4(v[4], v[5], v[6], v[7]));
+    }
 }
 
 // Register cap per segment width and tile height: the strip's samples and
@@ -352,7 +354,6 @@ fwd_chain_kernel(const FwdArgs a)
     using V = typename Md::V;
     using E = Edge<V, RT>;
     static_assert(RT == 2 || RT == 4 || RT == 8, "tiles of 2, 4 or 8 rows");
-    static_assert(RT != 8 || !CKPT, "8-row tiles have no checkpoints");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_query;
@@ -697,6 +698,10 @@ fwd_chain_kernel(const FwdArgs a)
                             __stcs(f4 + k * L, make_float4(prev[4 * k], prev[4 * k + 1], prev[4 * k + 2], prev[4 * k + 3]));
                         if constexpr (RT == 2) {
                             __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], diag, B, 0.f));
+                        } else if constexpr (RT == 8) {
+                            __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], A[3][W - 1]));
+                            __stcs(f4 + (W / 4 + 1) * L, make_float4(A[4][W - 1], A[5][W - 1], A[6][W - 1], diag));
+                            __stcs(f4 + (W / 4 + 2) * L, make_float4(B, 0.f, 0.f, 0.f));
                         } else {
                             __stcs(f4 + (W / 4) * L, make_float4(A[0][W - 1], A[1][W - 1], A[2][W - 1], diag));
                             __stcs(f4 + (W / 4 + 1) * L, make_float4(B, 0.f, 0.f, 0.f));

@@ -58,20 +58,21 @@ cudaError_t dispatch(sdtw_dtype dt, int W, int RT, bool ckpt, F&& f)
     case 32: return f(Inst<Tin, 32, RTv, CK>{});                          \
     default: return cudaErrorInvalidValue;                                \
     }
-#define SDTW_W8(Tin)                                                      \
+#define SDTW_W8(Tin, CK)                                                  \
     switch (W) {                                                          \
-    case 16: return f(Inst<Tin, 16, 8, false>{});                         \
-    case 20: return f(Inst<Tin, 20, 8, false>{});                         \
-    case 24: return f(Inst<Tin, 24, 8, false>{});                         \
-    case 28: return f(Inst<Tin, 28, 8, false>{});                         \
+    case 16: return f(Inst<Tin, 16, 8, CK>{});                            \
+    case 20: return f(Inst<Tin, 20, 8, CK>{});                            \
+    case 24: return f(Inst<Tin, 24, 8, CK>{});                            \
+    case 28: return f(Inst<Tin, 28, 8, CK>{});                            \
     default: return cudaErrorInvalidValue;                                \
     }
     if (RT == 8) {
-        // 8-row tiles: plain fills only (the per-step work of shuffles,
-        // conversions and loop control spread over 8 rows), W up to 28
+        // 8-row tiles (the per-step work of shuffles, conversions and loop
+        // control spread over 8 rows), W 16 to 28; with checkpoints FP32 only
+        if (dt == SDTW_F32 && ckpt) { SDTW_W8(float, true) }
         if (ckpt) return cudaErrorInvalidValue;
-        if (dt == SDTW_F16) { SDTW_W8(__half) }
-        if (dt == SDTW_F32) { SDTW_W8(float) }
+        if (dt == SDTW_F16) { SDTW_W8(__half, false) }
+        if (dt == SDTW_F32) { SDTW_W8(float, false) }
         return cudaErrorInvalidValue;
     }
     if (RT != 2 && RT != 4) return cudaErrorInvalidValue;
@@ -96,7 +97,7 @@ bool fwd_plan_supported(sdtw_dtype dt, int W, int RT, bool ckpt)
 {
     if (!fwd_width_supported(dt, W)) return false;
     if (RT == 2 || RT == 4) return true;
-    return RT == 8 && !ckpt && W >= 16 && W <= 28;
+    return RT == 8 && W >= 16 && W <= 28 && (!ckpt || dt == SDTW_F32);
 }
 
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT)

@@ -76,7 +76,7 @@ struct FwdArgs {
     float* colck;
     int64_t ck_slot;
     int32_t K;    // window width: column checkpoint stride (8 W)
-    int32_t ck_stride;      // steps between wavefront checkpoints: 16, 32 or 64
+    int32_t ck_stride;      // steps between wavefront checkpoints: 8, 16, 32 or 64
     int32_t rebase_period;  // steps between FP32 rebases: ckpt_rebase_period(stride) of the context's checkpointing plan, else kChunk
     float* ck_cost;
     int64_t* ck_end;
@@ -91,7 +91,7 @@ struct FwdPlan {
     int W = 16;          // segment width: reference columns per thread
     int P = 8;           // warps per query chain
     int RT = 2;          // query rows per thread per step (tile height: 2, 4, or 8 for the plain FP32 fill)
-    int KS = kChunk;     // with checkpoints: steps between wavefront checkpoints (16, 32 or 64)
+    int KS = kChunk;     // with checkpoints: steps between wavefront checkpoints (8, 16, 32 or 64)
     bool persistent = false;
     int grid = 0;
     int block = 0;
@@ -149,12 +149,12 @@ struct BwdArgs {
 // Checkpoint geometry of a forward plan (sdtw_forward.cu, sdtw_fill.cuh): floats of one
 // thread's record, wavefront checkpoints (one every KS steps) of the schedule
 // for a query of n rows, and the per-query slot sizes of the two checkpoint
-// arrays.  Checkpoint strides are 16, 32 or 64 steps; the checkpointing fill
+// arrays.  Checkpoint strides are 8, 16, 32 or 64 steps; the checkpointing fill
 // rebases every max(kChunk, KS) steps, so that no band of KS steps spans a
 // rebase.
-__host__ __device__ constexpr int fwd_record_floats(int RT) { return RT == 2 ? 4 : 8; }
-__host__ __device__ constexpr int ck_rows(int N) { return (N + 3) / 4 * 4; }
-constexpr bool ckpt_stride_supported(int KS) { return KS == 16 || KS == 32 || KS == 64; }
+__host__ __device__ constexpr int fwd_record_floats(int RT) { return RT == 2 ? 4 : RT == 4 ? 8 : 12; }
+__host__ __device__ constexpr int ck_rows(int N) { return (N + 7) / 8 * 8; }
+constexpr bool ckpt_stride_supported(int KS) { return KS == 8 || KS == 16 || KS == 32 || KS == 64; }
 constexpr int ckpt_rebase_period(int KS) { return KS > kChunk ? KS : kChunk; }
 int64_t fwd_ckpts(int64_t M, int n, int W, int P, int RT, int KS);
 int64_t fr_slot_floats(int64_t M, int N, int W, int P, int RT, int KS);

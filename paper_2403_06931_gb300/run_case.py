@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--seg-width", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--ckpt-stride", type=int, default=0, help="steps between wavefront checkpoints (16, 32, 64)")
+    ap.add_argument("--ckpt-stride", type=int, default=0, help="steps between wavefront checkpoints (8, 16, 32, 64)")
     ap.add_argument("--bwd-warps", type=int, default=0,
                     help="warps per query in the backward (1 = the walker alone; 0 = the library's choice)")
     ap.add_argument("--prune-gap", type=int, default=0,

@@ -154,10 +154,10 @@ def test_reserved_spin_limit_must_be_zero(lib):
 
 
 def test_checkpoint_strides_accepted_by_create(lib):
-    # 16, 32 and 64 steps are the strides the library has; any other positive
-    # stride is rejected before any device work (a negative one is invalid)
-    for ks, want in ((48, capi.SDTW_E_UNSUPPORTED), (8, capi.SDTW_E_UNSUPPORTED), (128, capi.SDTW_E_UNSUPPORTED),
-                     (-16, capi.SDTW_E_INVALID)):
+    # 8, 16, 32 and 64 steps are the strides the library has; any other
+    # positive stride is rejected before any device work (a negative one is invalid)
+    for ks, want in ((48, capi.SDTW_E_UNSUPPORTED), (4, capi.SDTW_E_UNSUPPORTED), (12, capi.SDTW_E_UNSUPPORTED),
+                     (128, capi.SDTW_E_UNSUPPORTED), (-16, capi.SDTW_E_INVALID)):
         cfg = capi.sdtw_config_init()
         cfg.ckpt_stride = ks
         cfg.flags = capi.SDTW_FLAG_GRAD
@@ -180,8 +180,9 @@ def test_backward_warps_range(lib):
         assert capi.sdtw_create(cfg)[0] == capi.SDTW_E_INVALID, v
 
 
-def test_eight_row_tiles_only_for_plain_fills_of_16_to_28_columns(lib):
-    for dtype, flags, width in ((capi.SDTW_F32, capi.SDTW_FLAG_GRAD, 0), (capi.SDTW_F32, 0, 32), (capi.SDTW_F32, 0, 8),
+def test_eight_row_tiles_only_for_16_to_28_columns(lib):
+    for dtype, flags, width in ((capi.SDTW_F32, capi.SDTW_FLAG_GRAD, 32), (capi.SDTW_F32, capi.SDTW_FLAG_GRAD, 8),
+                                (capi.SDTW_F32, 0, 32), (capi.SDTW_F32, 0, 8),
                                 (capi.SDTW_I8, 0, 32), (capi.SDTW_U8, 0, 8), (capi.SDTW_F16, 0, 32)):
         cfg = capi.sdtw_config_init()
         cfg.dtype = dtype

@@ -1,7 +1,7 @@
 """CPU model of the backward checkpoints and of the backward's band replay.
 
 The checkpointing forward (csrc/sdtw_fill.cuh) stores, every KS steps
-(KS = 16, 32 or 64), the state of its wavefront: each thread's latest row (its
+(KS = 8, 16, 32 or 64), the state of its wavefront: each thread's latest row (its
 strip of W columns, relative to the thread's integer base), the right-hand
 cells of its tile's other rows, its diagonal input and its base, as they stand
 before a rebase due at that step (the backward redoes that rebase; the fill
@@ -35,7 +35,7 @@ import pytest
 
 K_CHUNK = 32   # csrc/sdtw_internal.h kChunk
 REBASE_BELOW = 256.0   # csrc/sdtw_internal.h kRebaseBelow
-STRIDES = (16, 32, 64)   # checkpoint strides the library supports
+STRIDES = (8, 16, 32, 64)   # checkpoint strides the library supports
 INF = float("inf")
 
 
@@ -309,6 +309,8 @@ CASES = [
     (3, 4, 2, 61, 1500),    # three warps, partial last sweep
     (1, 4, 2, 160, 600),    # sweep period equal to the query's tiles (no idle steps)
     (1, 4, 4, 299, 500),    # the same with 4-row tiles and a ragged last tile
+    (2, 4, 8, 151, 700),    # 8-row tiles, ragged last tile
+    (1, 8, 8, 64, 900),     # 8-row tiles, the query shorter than the chain lag
 ]
 
 
@@ -391,7 +393,7 @@ def test_walk_through_bands_matches_full_matrix(P, W, RT, n, M, KS):
 def flat_checkpoints(fw, pl):
     """The forward's checkpoint arrays in their device layouts (one query)."""
     W, RT, L = pl.W, pl.RT, pl.L
-    E = 4 if RT == 2 else 8
+    E = record_floats(RT)
     fr = np.full(pl.ckpts * L * (W + E), np.nan)
     for (c, tau), (prev, alast, diag, B) in fw["frontier"].items():
         base = c * L * (W + E)
@@ -402,11 +404,23 @@ def flat_checkpoints(fw, pl):
         for e in range(E):
             fr[base + ((W // 4 + e // 4) * L + tau) * 4 + e % 4] = rec[e]
     nwin = -(-pl.M // pl.K)
-    rows = -(-pl.n // 4) * 4            # windows are padded to a multiple of 4 rows
+    rows = ck_rows(pl.n)
     ck = np.full(max(0, nwin - 1) * rows, np.nan)
     for (b, i), v in fw["colck"].items():
         ck[(b - 1) * rows + i] = v
     return fr, ck
+
+
+def record_floats(RT):
+    """Floats of a thread's checkpoint record (csrc/sdtw_internal.h
+    fwd_record_floats): RT-1 right-hand cells, diag and base, in float4s."""
+    return {2: 4, 4: 8, 8: 12}[RT]
+
+
+def ck_rows(n):
+    """Rows of a window's boundary column (csrc/sdtw_internal.h ck_rows):
+    padded to a multiple of 8, so an 8-row tile's store stays in its window."""
+    return -(-n // 8) * 8
 
 
 def rows_per_step(RT):
@@ -420,7 +434,7 @@ def kernel_backward(fw, pl, end, RS=None):
     RS = rows_per_step(pl.RT) if RS is None else RS
     n, M, W, RT, L, S, Pp, nt = pl.n, pl.M, pl.W, pl.RT, pl.L, pl.S, pl.Pp, pl.nt
     WB, KW, KC = W // 4, 32 * (W // 4), pl.KS     # KC: a band's height in steps
-    E = 4 if RT == 2 else 8
+    E = record_floats(RT)
     fr, ck = flat_checkpoints(fw, pl)
     xs, ys_all = fw["x"], fw["y"]
     lag = lambda tau: (tau >> 5) * (32 + K_CHUNK) + (tau & 31)  # noqa: E731
@@ -442,7 +456,7 @@ def kernel_backward(fw, pl, end, RS=None):
         rf0 = RT * max(0, ps0)
         re0 = min(min(n, RT * min(nt, ps0 + KC)), wi + 1)
         ys = [ys_all[c0 + k] if c0 + k < M else 0.0 for k in range(KW)]
-        lcol = [ck[(b - 1) * (-(-n // 4) * 4) + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
+        lcol = [ck[(b - 1) * ck_rows(n) + rf0 + k] for k in range(re0 - rf0)] if b > 0 else []
         frc = c * L * (W + E)
         redo = (c * KC) % pl.R == 0       # a rebase was due at the band's first step
         rb = (lambda B0, f: rebase(B0, f)) if redo else (lambda B0, f: (B0, 0.0))  # noqa: E731
@@ -453,10 +467,10 @@ def kernel_backward(fw, pl, end, RS=None):
             d, sub = lane >> 2, lane & 3
             ps = ps0 - d
             st = dict(d=d, sub=sub, ps=ps, rf=RT * max(0, ps), re=min(n, RT * min(nt, ps + KC)),
-                      rf_left=RT * max(0, ps + 1), e=[0.0] * 4, dd=0.0)
+                      rf_left=RT * max(0, ps + 1), e=[0.0] * RT, dd=0.0)
             tau = tau0 + d
             if 1 <= ps <= nt:
-                Bn, dl = rb(rec_at(2 if RT == 2 else 4, tau), fr_at(0, tau))
+                Bn, dl = rb(rec_at(RT, tau), fr_at(0, tau))
                 st["D"] = [r32(fr_at(sub * WB + k, tau) - dl) for k in range(WB)]
                 st["B"] = Bn
                 st["dg"] = r32((rec_at(RT - 1, tau) if sub == 0 else fr_at(sub * WB - 1, tau)) - dl)
@@ -465,11 +479,8 @@ def kernel_backward(fw, pl, end, RS=None):
             st["bsrc"] = 0.0
             if sub == 0 and d >= 1:
                 if 1 <= ps + 1 <= nt:
-                    st["bsrc"], dl = rb(rec_at(2 if RT == 2 else 4, tau - 1), fr_at(0, tau - 1))
-                    if RT == 2:
-                        e = [rec_at(0, tau - 1), fr_at(W - 1, tau - 1), 0.0, 0.0]
-                    else:
-                        e = [rec_at(0, tau - 1), rec_at(1, tau - 1), rec_at(2, tau - 1), fr_at(W - 1, tau - 1)]
+                    st["bsrc"], dl = rb(rec_at(RT, tau - 1), fr_at(0, tau - 1))
+                    e = [rec_at(h, tau - 1) for h in range(RT - 1)] + [fr_at(W - 1, tau - 1)]
                     st["e"] = [r32(v - dl) for v in e]
             st["btile"], st["dltile"] = st["B"], 0.0
             st["y"] = ys[lane * WB:(lane + 1) * WB]
@@ -596,6 +607,8 @@ KERNEL_CASES = [
     (1, 4, 4, 299, 500),
     (2, 8, 4, 97, 1300),
     (1, 8, 4, 150, 800),    # the last tile holds two of the query's rows
+    (2, 4, 8, 151, 700),    # 8-row tiles: the band's tilt equals the lane chain's
+    (1, 8, 8, 150, 800),    # ... the last tile holds six of the query's rows
 ]
 
 
@@ -603,8 +616,8 @@ KERNEL_CASES = [
 @pytest.mark.parametrize("two_rows", [False, True])
 @pytest.mark.parametrize("P,W,RT,n,M", KERNEL_CASES)
 def test_kernel_band_schedule_and_walk(P, W, RT, n, M, two_rows, KS):
-    """Both step heights a band of 4-row tiles can take (2 rows or the tile),
-    every checkpoint stride."""
+    """Both step heights a band of 4- or 8-row tiles can take (2 rows or the
+    tile), every checkpoint stride."""
     if two_rows and RT == 2:
         pytest.skip("2-row tiles take 2-row steps")
     pl, fw = _setup(P, W, RT, n, M, seed=n * 13 + M, KS=KS)
@@ -621,7 +634,7 @@ def test_kernel_schedule_random_shapes():
     the end cell is recomputed bit for bit."""
     rng = np.random.default_rng(4242)
     for _ in range(24):
-        P, W, RT = int(rng.choice([1, 2])), int(rng.choice([4, 8])), int(rng.choice([2, 4]))
+        P, W, RT = int(rng.choice([1, 2])), int(rng.choice([4, 8])), int(rng.choice([2, 4, 8]))
         RS = int(rng.choice([1, 2, RT]))
         KS = int(rng.choice(STRIDES))
         n, M = int(rng.integers(1, 240)), int(rng.integers(2, 1300))
@@ -645,7 +658,7 @@ def _stretched(seed, M=1400, step=8, n=150, scale=8.0):
 
 
 @pytest.mark.parametrize("KS", STRIDES)
-@pytest.mark.parametrize("P,W,RT", [(1, 4, 2), (2, 4, 4), (1, 8, 4)])
+@pytest.mark.parametrize("P,W,RT", [(1, 4, 2), (2, 4, 4), (1, 8, 4), (1, 4, 8)])
 def test_rebase_to_low_left_inputs_is_replayed(P, W, RT, KS):
     """With many rebases to low left inputs: every band replays bit for bit,
     and the lane schedule's walk equals the walk over the whole FP32 matrix."""
@@ -674,8 +687,8 @@ def _dir_rows(RT, KS, RS=2):
     return RS * (most - RT * 7 // RS)
 
 
-@pytest.mark.parametrize("RT", [2, 4])
-@pytest.mark.parametrize("KS", [16, 32, 64])
+@pytest.mark.parametrize("RT", [2, 4, 8])
+@pytest.mark.parametrize("KS", STRIDES)
 def test_band_slot_rows_bound(RT, KS):
     # the backward's lane schedule for a band: lane l (strip d = l // 4) has rows
     # [rf, hi) and handles row r at step (r - rtop) / RS + l; the band starts at

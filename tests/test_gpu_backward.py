@@ -132,7 +132,9 @@ def test_walkback_tie_rule_on_many_queries(gpu):
 @pytest.mark.parametrize("B,N,M,W,RT,P", [(4, 50, 700, 8, 2, 1), (3, 300, 2000, 16, 4, 2), (2, 129, 5000, 32, 2, 4),
                                           (3, 1, 300, 8, 4, 2), (2, 40, 1, 8, 2, 1), (2, 700, 600, 16, 2, 1),
                                           (2, 600, 3000, 24, 4, 4), (3, 257, 1100, 24, 2, 3),
-                                          (2, 1000, 40000, 24, 4, 4), (2, 333, 20000, 32, 4, 8)])
+                                          (2, 1000, 40000, 24, 4, 4), (2, 333, 20000, 32, 4, 8),
+                                          (3, 1, 300, 16, 8, 2), (2, 600, 3000, 24, 8, 4), (3, 257, 1100, 16, 8, 3),
+                                          (2, 1000, 40000, 20, 8, 4), (2, 333, 20000, 28, 8, 8)])
 def test_backward_shapes(gpu, B, N, M, W, RT, P):
     # band replays across warps, sweeps, ragged last tiles, a one-row query,
     # a one-column reference and queries longer than the reference
@@ -144,20 +146,22 @@ def test_backward_shapes(gpu, B, N, M, W, RT, P):
 
 
 @pytest.mark.parametrize("P", [2, 5])
-@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("RT", [2, 4, 8])
 @pytest.mark.parametrize("W", [8, 16, 20, 24, 28, 32])
 def test_backward_every_tile_height_and_width(gpu, RT, W, P):
     # checkpoints taken by every checkpointing forward variant
+    if RT == 8 and not 16 <= W <= 28:
+        pytest.skip("8-row tiles take 16 to 28 columns")
     w = inputs.tiny(B=3, N=700, M=9000, seed=400 + RT + W)
     cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=W, tile_rows=RT, warps_per_query=P)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
 
-@pytest.mark.parametrize("KS", [16, 32, 64])
-@pytest.mark.parametrize("RT", [2, 4])
+@pytest.mark.parametrize("KS", [8, 16, 32, 64])
+@pytest.mark.parametrize("RT", [2, 4, 8])
 def test_backward_every_checkpoint_stride(gpu, RT, KS):
-    # bands of 16, 32 or 64 forward steps, with several warps and sweeps
+    # bands of 8, 16, 32 or 64 forward steps, with several warps and sweeps
     w = inputs.tiny(B=4, N=600, M=12000, seed=430 + RT + KS)
     cost, end, gq, gr, path, g = run_bwd(gpu, w, seg_width=24, tile_rows=RT, warps_per_query=3, ckpt_stride=KS)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
@@ -165,13 +169,14 @@ def test_backward_every_checkpoint_stride(gpu, RT, KS):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * max(np.abs(gy_sum).max(), 1.0) + 1e-6)
 
 
-@pytest.mark.parametrize("KS", [16, 32, 64])
-def test_backward_stretched_paths(gpu, KS):
+@pytest.mark.parametrize("KS", [8, 16, 32, 64])
+@pytest.mark.parametrize("RT", [4, 8])
+def test_backward_stretched_paths(gpu, KS, RT):
     # long horizontal runs, scaled so that costs reach the forward's rebase to
     # low left inputs: the backward must replay every such rebase to reproduce
     # the forward's values (the device checks the end cell bit for bit)
     w = inputs.stretched(B=8, N=300, M=30000, scale=8.0)
-    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=KS)
+    cost, end, gq, gr, path, g = run_bwd(gpu, w, ckpt_stride=KS, tile_rows=RT, seg_width=32 if RT == 4 else 28)
     oc, _ = oracle.forward_batch(w.ref, w.queries)
     check_validity(w, cost, end, gq, gr, path, g, range(w.B), oc)
 
@@ -193,13 +198,14 @@ def test_backward_ragged(gpu):
     assert np.all(np.abs(gr - gy_sum) <= GTOL * np.abs(gy_sum).max() + 1e-6)
 
 
-@pytest.mark.parametrize("case", ["stretched16", "stretched64", "tiny_rt2", "w8", "ragged", "vertical"])
+@pytest.mark.parametrize("case", ["stretched16", "stretched64", "stretched_rt8", "tiny_rt2", "w8", "ragged", "vertical"])
 def test_backward_helpers_give_identical_results(gpu, case):
     # the walker alone (bwd_warps=1) and with 1 to 3 helpers recomputing the
     # predicted bands: the same path, gradients and reference gradient, bit for bit
     w, st = {
         "stretched16": (inputs.stretched(B=6, N=300, M=30000, scale=8.0), dict(ckpt_stride=16)),
         "stretched64": (inputs.stretched(B=4, N=300, M=30000), dict(ckpt_stride=64, tile_rows=2)),
+        "stretched_rt8": (inputs.stretched(B=6, N=300, M=30000, scale=8.0), dict(ckpt_stride=8, tile_rows=8)),
         "tiny_rt2": (inputs.tiny(B=5, N=500, M=8000, seed=91), dict(seg_width=24, tile_rows=2, warps_per_query=3)),
         "w8": (inputs.tiny(B=4, N=400, M=6000, seed=92), dict(seg_width=8, tile_rows=4, warps_per_query=2)),
         "ragged": (inputs.ragged_fp32(B=9, n_lo=1, n_hi=500, M=7000, seed=93), {}),
@@ -233,19 +239,19 @@ def test_walker_wait_runs_out_when_helpers_never_answer(gpu):
 
 def _ckpt_floats_per_query(M, N, W, P, RT, KS):
     """Backward workspace per query (floats) of a checkpointing plan: the
-    wavefront slot (one record of W + 4 or W + 8 floats per thread and
-    checkpoint, one checkpoint every KS steps), the boundary columns every 8 W
-    columns (rows padded to 4), a gradient row and 7 scalars (the layout the
-    library documents)."""
+    wavefront slot (one record of W + 4, W + 8 or W + 12 floats per thread and
+    checkpoint for 2-, 4- or 8-row tiles, one checkpoint every KS steps), the
+    boundary columns every 8 W columns (rows padded to 8), a gradient row and
+    7 scalars (the layout the library documents)."""
     S, lag_last = 32 * P * W, (P - 1) * 64 + 31
     nsw, nt = -(-M // S), -(-N // RT)
     total = (nsw - 1) * max(nt, lag_last + 32) + nt + lag_last
-    fr = -(-total // KS) * 32 * P * (W + (4 if RT == 2 else 8))
-    ck = (-(-M // (8 * W)) - 1) * (-(-N // 4) * 4)
+    fr = -(-total // KS) * 32 * P * (W + {2: 4, 4: 8, 8: 12}[RT])
+    ck = (-(-M // (8 * W)) - 1) * (-(-N // 8) * 8)
     return fr + ck + M + 7
 
 
-@pytest.mark.parametrize("KS", [16, 32, 64])
+@pytest.mark.parametrize("KS", [8, 16, 32, 64])
 def test_chunked_and_recomputed_backward_are_identical(gpu, KS):
     w = inputs.tiny(B=9, N=200, M=4000, seed=81)
     st = dict(seg_width=16, tile_rows=4, warps_per_query=2, ckpt_stride=KS)
