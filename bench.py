@@ -45,10 +45,18 @@ L2_FLUSH_BYTES = 512 << 20
 # reported as null).  Captured on 128 of the 512 queries (the writes are the
 # per-query checkpoints) and scaled by 4 to the 512-query launch;
 # profiles/fwd_chain_kernel_f32_ckpt_W32_RT4_KS16_paper_512x2000_vs_100000.md
-FWD_SRC_SHA = "f2eb11686c846bca"
+FWD_SRC_SHA = "54359229b4890b5f"
 FWD_TRAFFIC_BYTES = {
-    (32, 4, 4, 16): 4 * (2_444_288 + 2_387_886_848),
-    (32, 4, 4, 32): 4 * (1_959_424 + 1_363_876_864),
+    (32, 4, 4, 16): 4 * (2_547_968 + 2_388_259_840),
+    (32, 4, 4, 32): 4 * (2_154_240 + 1_364_210_432),
+    (28, 8, 4, 16): 4 * (8_784_640 + 1_548_449_792),
+    (28, 8, 4, 8): 4 * (17_545_984 + 2_702_749_952),
+    (28, 4, 4, 32): 4 * (2_135_296 + 1_429_650_432),
+    (28, 4, 4, 16): 4 * (2_383_360 + 2_460_893_696),
+    (32, 4, 4, 8): 4 * (3_400_704 + 4_436_850_944),
+    (28, 8, 4, 32): 4 * (4_549_888 + 971_104_768),
+    (24, 8, 4, 16): 4 * (9_507_584 + 1_694_594_048),
+    (24, 8, 4, 8): 4 * (21_463_808 + 2_920_252_928),
 }
 
 

@@ -703,9 +703,14 @@ __global__ void __launch_bounds__(32 * kMaxSlots) bwd_band_kernel(const BwdArgs 
                     }
                 }
             }
+            // the first lane whose cell leaves the row, and its code, from ballots
+            // (a shuffle of the code would add its latency to the walk's chain)
             const unsigned stop = __ballot_sync(0xffffffffu, code != kLeft);
-            const int f = stop ? __ffs(stop) - 1 : 32;        // first lane whose cell leaves the row
-            const int fcode = f < 32 ? __shfl_sync(0xffffffffu, code, f) : kLeft;
+            const unsigned bdiag = __ballot_sync(0xffffffffu, code == kDiag);
+            const unsigned bup = __ballot_sync(0xffffffffu, code == kUp);
+            const int f = stop ? __ffs(stop) - 1 : 32;
+            const unsigned fbit = stop & (0u - stop);
+            const int fcode = !stop ? kLeft : (bdiag & fbit) ? kDiag : (bup & fbit) ? kUp : kOutside;
             const int last = fcode == kOutside ? f - 1 : (f < 32 ? f : 31);  // last lane on the path
             const bool on = lane <= last;
             const float cg = on ? g2 * (xi - ys[jk - c0]) : 0.f;
