@@ -87,6 +87,58 @@ template <int WB, int RS, bool EXACT>
 __device__ __forceinline__ void tile_rows(float (&D)[WB], const float (&y)[WB], const float (&x)[RS], float (&l)[RS],
                                           float dg, int v, uint32_t (&nd)[RS], uint32_t (&nu)[RS])
 {
+    if constexpr (RS == 2) {
+        // The cells (0, k) and (1, k-1) lie on one anti-diagonal and are
+        // independent: their multiply-adds run as one f32x2 FMA (each lane
+        // rounded once, exactly as fmaf), the same values as cell by cell.
+        // Row 0 at column k: up D[k], diagonal g0, left l0; row 1 at column
+        // k-1: up (row 0 at k-1) l0, diagonal g1, left l1.  Choice bits as
+        // below.
+        uint32_t nd0 = 0u, nu0 = 0u, nd1 = 0u, nu1 = 0u;
+        float g0 = dg, l0 = l[0], g1 = l[0], l1 = l[1];
+        {
+            const float u0 = D[0];
+            const float m0 = min3_f32(u0, g0, l0);
+            nd0 |= m0 != g0 ? 1u : 0u;
+            nu0 |= m0 != l0 ? 1u : 0u;
+            const float t0 = x[0] - y[0];
+            g0 = u0;
+            l0 = fmaf(t0, t0, m0);
+        }
+#pragma unroll
+        for (int k = 1; k < WB; ++k) {
+            const float u0 = D[k], u1 = l0;
+            const float m0 = min3_f32(u0, g0, l0);
+            const float m1 = min3_f32(u1, g1, l1);
+            nd0 |= m0 != g0 ? (1u << k) : 0u;
+            nu0 |= m0 != l0 ? (1u << k) : 0u;
+            nd1 |= m1 != g1 ? (1u << (k - 1)) : 0u;
+            nu1 |= m1 != l1 ? (1u << (k - 1)) : 0u;
+            const float2 t = make_float2(x[0] - y[k], x[1] - y[k - 1]);
+            const float2 nv = __ffma2_rn(t, t, make_float2(m0, m1));
+            D[k - 1] = EXACT && v < 2 ? u1 : nv.y;  // the last valid row
+            g0 = u0;
+            l0 = nv.x;
+            g1 = u1;
+            l1 = nv.y;
+        }
+        {
+            const float u1 = l0;
+            const float m1 = min3_f32(u1, g1, l1);
+            nd1 |= m1 != g1 ? (1u << (WB - 1)) : 0u;
+            nu1 |= m1 != l1 ? (1u << (WB - 1)) : 0u;
+            const float t1 = x[1] - y[WB - 1];
+            l1 = fmaf(t1, t1, m1);
+            D[WB - 1] = EXACT && v < 2 ? u1 : l1;
+        }
+        l[0] = l0;
+        l[1] = l1;
+        nd[0] = nd0;
+        nu[0] = nu0;
+        nd[1] = nd1;
+        nu[1] = nu1;
+        return;
+    }
     float dgs[RS];
     dgs[0] = dg;
 #pragma unroll
@@ -99,12 +151,13 @@ __device__ __forceinline__ void tile_rows(float (&D)[WB], const float (&y)[WB], 
         float row_v = up;
 #pragma unroll
         for (int h = 0; h < RS; ++h) {
-            // bit k of nd: the minimum is not the diagonal; of nu: neither the
-            // diagonal nor the left cell (the cell above).  Written as selects:
-            // branches here stall a warp that runs alone on its scheduler.
+            // bit k of nd: the minimum is not the diagonal; of nu: it is not the
+            // left cell (the walk reads nu only where nd is set, so there nu
+            // means the cell above).  Written as selects: branches here stall a
+            // warp that runs alone on its scheduler.
             const float m = min3_f32(up, dgs[h], l[h]);
             const bool not_diag = m != dgs[h];
-            const bool is_up = not_diag & (m != l[h]);
+            const bool is_up = m != l[h];
             nd[h] |= not_diag ? (1u << k) : 0u;
             nu[h] |= is_up ? (1u << k) : 0u;
             const float t = x[h] - y[k];
