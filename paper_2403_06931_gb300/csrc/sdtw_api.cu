@@ -154,7 +154,8 @@ FwdPlan default_fwd_plan(const sdtw_ctx* c, int B, int N, int64_t M, bool ragged
     // fills with 8-row tiles of 24 columns (FP32, binary16) or 28 (the integer
     // modes; with pruning 4-row tiles, 22% faster there); the fill with
     // checkpoints with 4-row tiles of 32 columns (the backward's wider windows
-    // give fewer band changes)
+    // give fewer band changes; its 8-row plans, W 16 to 28, are the
+    // autotuner's to choose)
     FwdPlan p;
     p.W = c->cfg.seg_width > 0 ? c->cfg.seg_width
                                : (ckpt ? (c->cfg.tile_rows == 8 ? 28 : 32) : int_mode(c->cfg.dtype) ? 28 : 24);

@@ -8,7 +8,7 @@
 // W consecutive reference columns (the paper's "segment", Section 5.2) and
 // keeps the strip's reference samples and its latest DP row in registers.  At
 // every step a thread advances its strip by RT query rows (an RT x W register
-// tile, RT = 2 or 4), and thread l runs one step behind thread l-1, so one
+// tile, RT = 2, 4 or 8), and thread l runs one step behind thread l-1, so one
 // step fills an anti-diagonal of tiles.  Inside the tile, cell j of row r and
 // cell j-1 of row r+1 are independent, so each thread runs RT dependency
 // chains; the tile's first RT-1 rows go to short-lived scratch registers and

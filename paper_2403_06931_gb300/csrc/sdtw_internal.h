@@ -101,7 +101,7 @@ struct FwdPlan {
 // Forward launch (sdtw_forward.cu).
 bool fwd_width_supported(sdtw_dtype dt, int W);
 // a (W, RT) the fill has an instantiation for: RT 2 or 4 for every mode, RT 8
-// for the plain FP32 fill at W 16..28
+// at W 16..28 for the plain fills and the FP32 fill with checkpoints
 bool fwd_plan_supported(sdtw_dtype dt, int W, int RT, bool ckpt);
 int64_t fwd_smem_bytes(sdtw_dtype dt, int64_t N, int P, int W, int RT);
 // 0 when smem exceeds kMaxSmemBytes or the plan cannot be resident
