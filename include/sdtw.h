@@ -102,7 +102,8 @@ typedef struct sdtw_config {
                                     or 32; 0 = chosen by the library */
     int32_t warps_per_query;     /* warps cooperating on one query; 0 = chosen by the library */
     int32_t ckpt_stride;         /* forward steps between backward wavefront checkpoints: 8, 16, 32 or 64; 0 = chosen by
-                                    the library (16, or the autotuner's choice) */
+                                    the library (16 with 4-row tiles, 8 with 8-row tiles, or the autotuner's
+                                    choice) */
     int32_t prune_gap;           /* SDTW_I8 / SDTW_U8 only: 0 = off (exact); > 0 = early-INF pruning (paper
                                     Section 8, opt-in, changes results): a cell whose two samples differ by more
                                     than prune_gap costs +inf, and +inf absorbs every sum; a query with no path
