@@ -720,3 +720,79 @@ def test_band_slot_rows_bound(RT, KS):
                     assert need <= bound, (RT, KS, n, ps0, wi, dj, need, bound)
                     worst = max(worst, need)
     assert worst == bound
+
+
+# ---------------------------------------------------------------------------
+# The band recompute's two-row lane step (csrc/sdtw_backward.cu tile_rows) runs
+# the cells (0, k) and (1, k-1) of one anti-diagonal together, their two
+# multiply-adds as one f32x2 FMA.  The model below follows that order and must
+# give the cell-by-cell step's values, last-column left inputs and choice bits.
+
+def _two_row_step_by_cells(D, y, x, l, dg, v, exact):
+    D, l = list(D), list(l)
+    dgs = [dg, l[0]]
+    nd, nu = [0, 0], [0, 0]
+    for k in range(len(D)):
+        up, row_v = D[k], D[k]
+        for h in range(2):
+            m = min(up, dgs[h], l[h])
+            nd[h] |= (1 << k) if m != dgs[h] else 0
+            nu[h] |= (1 << k) if m != l[h] else 0
+            t = r32(x[h] - y[k])
+            nv = fma32(t, t, m)
+            dgs[h], l[h], up = up, nv, nv
+            if exact and h < v:
+                row_v = nv
+        D[k] = row_v if exact else up
+    return D, l, nd, nu
+
+
+def _two_row_step_by_antidiagonals(D, y, x, l, dg, v, exact):
+    D, WB = list(D), len(D)
+    nd0 = nu0 = nd1 = nu1 = 0
+    g0, l0, g1, l1 = dg, l[0], l[0], l[1]
+    u0 = D[0]
+    m0 = min(u0, g0, l0)
+    nd0 |= 1 if m0 != g0 else 0
+    nu0 |= 1 if m0 != l0 else 0
+    t0 = r32(x[0] - y[0])
+    g0, l0 = u0, fma32(t0, t0, m0)
+    for k in range(1, WB):
+        u0, u1 = D[k], l0
+        m0, m1 = min(u0, g0, l0), min(u1, g1, l1)
+        nd0 |= (1 << k) if m0 != g0 else 0
+        nu0 |= (1 << k) if m0 != l0 else 0
+        nd1 |= (1 << (k - 1)) if m1 != g1 else 0
+        nu1 |= (1 << (k - 1)) if m1 != l1 else 0
+        ta, tb = r32(x[0] - y[k]), r32(x[1] - y[k - 1])
+        na, nb = fma32(ta, ta, m0), fma32(tb, tb, m1)   # the two lanes of one f32x2 FMA
+        D[k - 1] = u1 if (exact and v < 2) else nb
+        g0, l0, g1, l1 = u0, na, u1, nb
+    u1 = l0
+    m1 = min(u1, g1, l1)
+    nd1 |= (1 << (WB - 1)) if m1 != g1 else 0
+    nu1 |= (1 << (WB - 1)) if m1 != l1 else 0
+    t1 = r32(x[1] - y[WB - 1])
+    l1 = fma32(t1, t1, m1)
+    D[WB - 1] = u1 if (exact and v < 2) else l1
+    return D, [l0, l1], [nd0, nd1], [nu0, nu1]
+
+
+def test_two_row_step_pairs_anti_diagonals():
+    rng = np.random.default_rng(2718)
+    for _ in range(3000):
+        WB = int(rng.choice([2, 4, 5, 6, 7, 8]))
+        ties = bool(rng.integers(0, 2))   # integer-valued inputs make exact ties common
+
+        def vals(n, nonneg=False):
+            a = rng.standard_normal(n) * 3
+            a = np.round(a) if ties else a
+            return [r32(abs(float(t)) if nonneg else float(t)) for t in a]
+        D, y, x, l = vals(WB, True), vals(WB), vals(2), vals(2, True)
+        dg = vals(1, True)[0]
+        if rng.random() < 0.1:
+            l[0] = INF                     # the window's first strip above the query
+        v, exact = int(rng.integers(1, 3)), bool(rng.integers(0, 2))
+        a = _two_row_step_by_cells(D, y, x, l, dg, v, exact)
+        b = _two_row_step_by_antidiagonals(D, y, x, l, dg, v, exact)
+        assert a == b, (WB, v, exact)
